@@ -1,0 +1,137 @@
+/* fhmg -- multigrid waveform relaxation with an H-matrix time operator for the
+ * time-fractional heat equation, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Hu, Rodrigo & Gaspar, "Using hierarchical matrices in the solution of the
+ * time-fractional heat equation by multigrid waveform relaxation" (arXiv 1706.07632).
+ *
+ * The discrete problem (Section 2, Eqs. discrete_model_IVP_1-3) couples M time levels
+ * t_m = T (m/M)^gamma (m = 1..M) and N^dim interior spatial points (dim = 1 or 2, grid size
+ * h = Lx/(N+1), homogeneous Dirichlet boundaries):
+ *
+ *     sum_{j<=m} R_{m,j} u_{.,j} + A_h u_{.,m} = f_{.,m} + d_{m,m} g,
+ *
+ * R the Petrov-Galerkin L1 matrix of the Caputo derivative of order alpha (Eq.
+ * elements_matrix_R), A_h the 3-point / 5-point negative Laplacian, g the initial data.
+ *
+ * Conventions shared by every entry point:
+ *  - Grid functions (u, f, residuals, corrections) are caller-owned DEVICE arrays of doubles,
+ *    time-major with space contiguous: element (m, p) at m * N^dim + p, m = 0..M-1 for t_1..t_M,
+ *    p = n - 1 (1D) or p = iy * N + ix (2D).  g is a device array of N^dim doubles or NULL (= 0).
+ *  - Every call is ordered on the problem's stream and returns before the GPU work ends unless
+ *    it returns a host value (norms, cycle counts), in which case it synchronises the stream.
+ *  - Every function returns an fhmg_status and never aborts; arguments are validated on the
+ *    host.  Outputs are written only on FHMG_OK, except u after a solve that did not reach
+ *    rtol, which holds the last iterate.  The library never frees caller memory.
+ *  - fhmg_last_error() returns a message for the last failure of the calling thread.
+ */
+#ifndef FHMG_H_
+#define FHMG_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fhmg_hmatrix_s* fhmg_hmatrix; /* opaque; host-side H-matrix, library-owned */
+typedef struct fhmg_problem_s* fhmg_problem; /* opaque; device data + workspaces, library-owned */
+
+enum fhmg_status {
+  FHMG_OK = 0,
+  FHMG_EINVAL = -1,   /* invalid argument (message in fhmg_last_error) */
+  FHMG_ECUDA = -2,    /* a CUDA call failed */
+  FHMG_ENOMEM = -3,   /* device or host allocation failed */
+  FHMG_ENOTCONV = -4, /* solve stopped at max_cycles above rtol (u holds the last iterate) */
+  FHMG_ENAN = -5,     /* a residual norm was NaN or Inf */
+  FHMG_ETIMEOUT = -6  /* a bounded device wait gave up */
+};
+
+enum fhmg_prec {
+  FHMG_FP64 = 0,       /* every product in FP64 */
+  FHMG_MIXED_FP32 = 1  /* defect correction: FP64 residual, FP32 inner V-cycles */
+};
+
+const char* fhmg_last_error(void);
+
+/* Builds the time operator (host, one-time).  Section 2: mesh t_m = T (m/M)^gamma and the
+ * L1 matrix R; Section 3: its H-matrix form (index bisection, Definition 3.1 admissibility,
+ * Taylor degenerate kernel Eqs. A_elements / B_elements).
+ *   alpha in (0,1): fractional order (the paper's delta); gamma >= 1: grading exponent (the
+ *   paper's r); T > 0: final time; M: time steps, M = leaf * 2^p; leaf in {16, 32, 64}
+ *   (leaf > M means one leaf of size M);
+ *   rank > 0: k Taylor terms per admissible block, no recompression (the paper's form);
+ *   rank == 0 and tol > 0: Taylor terms from the Theorem 3.1 bound, then each block
+ *     recompressed (QR + SVD) to singular values > tol * (largest of the block);
+ *   rank == 0 and tol == 0: dense lower-triangular R (no low-rank blocks).
+ * On success *out owns host memory released by fhmg_hmatrix_destroy. */
+int fhmg_build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,
+                       fhmg_hmatrix* out);
+/* Block counts, largest rank and bytes of the FP64 device representation. Any pointer may be NULL. */
+int fhmg_hmatrix_info(fhmg_hmatrix h, int* n_dense, int* n_lowrank, int* max_rank, size_t* bytes);
+/* Copies the mesh t_0..t_M (M+1 host doubles) and the initial-data weights d_{m,m} (M host
+ * doubles); either pointer may be NULL. */
+int fhmg_hmatrix_mesh(fhmg_hmatrix h, double* t_out, double* dmm_out);
+/* Writes the approximated matrix R~ densely (M*M host doubles, row-major, upper part zero). */
+int fhmg_hmatrix_dense(fhmg_hmatrix h, double* R_out);
+/* Algorithmic FP64 flops of one H-matvec (Algorithm 3) or line solve (Algorithm 4) per column. */
+int fhmg_hmatrix_flops(fhmg_hmatrix h, double* flops_per_column);
+int fhmg_hmatrix_destroy(fhmg_hmatrix h);
+
+/* Creates a problem on the current CUDA device: dim in {1,2}; N = 2^levels - 1 interior points
+ * per dimension (levels >= 1); Lx > 0 domain length; prec an fhmg_prec; stream a cudaStream_t
+ * (NULL = legacy default stream).  Uploads the H-matrix, builds the per-level inverted diagonal
+ * leaves (D_ii + s_l I)^{-1}, s_l = 2/h_l^2 (1D) or 4/h_l^2 (2D), and allocates workspaces.
+ * The problem keeps a reference to h; destroy the problem before h. */
+int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, void* stream,
+                        fhmg_problem* out);
+int fhmg_problem_destroy(fhmg_problem p);
+/* Chooses the column tile of each kernel by timing (autotuner); optional. */
+int fhmg_problem_autotune(fhmg_problem p);
+/* Resets the counters below and, if enable != 0, records CUDA events on the problem's stream
+ * around every smoother launch on the finest grid (the dominant kernel). */
+int fhmg_problem_profile(fhmg_problem p, int enable);
+/* Synchronises the stream and reports, since the last fhmg_problem_profile: the number of
+ * kernel launches issued, the number of finest-grid smoother launches timed and their summed
+ * device time in milliseconds.  Any pointer may be NULL. */
+int fhmg_problem_counters(fhmg_problem p, long long* launches, long long* smooth_launches, double* smooth_ms);
+
+/* --- the hot-path steps, exposed one by one (each is one or more kernel launches) --- */
+
+/* Algorithm 4 over many columns: X = (R~ + s_level I)^{-1} B; X, B device [M][ncols]
+ * (time-major, column-contiguous); level 0..levels-1 selects the shift (level levels-1 is the
+ * finest grid).  X may alias B. */
+int fhmg_line_solve(fhmg_problem p, int level, double* X, const double* B, long long ncols);
+/* Algorithm 3 over many columns: Y = R~ X; device [M][ncols]; Y must not alias X. */
+int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols);
+/* nsweeps red-black zebra-in-time sweeps (Section 4) on the finest grid: u updated in place,
+ * F the full right-hand side (f + d_{m,m} g). */
+int fhmg_smooth(fhmg_problem p, double* u, const double* F, int nsweeps);
+/* Defect r = f + d_{m,m} g - (R~ (x) I) u - (I (x) A_h) u on the finest grid, all points. */
+int fhmg_residual(fhmg_problem p, const double* u, const double* f, const double* g, double* r_out);
+/* Full-weighting restriction of the defect to the next coarser grid (Algorithm 2), computed as
+ * FW(F - A_h u) - R~ FW(u); rc_out is device [M][Nc^dim], Nc = (N-1)/2. */
+int fhmg_restrict_residual(fhmg_problem p, const double* u, const double* F, double* rc_out);
+/* u += I_{2h}^h e (linear / bilinear interpolation in space, Algorithm 2); e is [M][Nc^dim]. */
+int fhmg_prolong_correct(fhmg_problem p, double* u, const double* e);
+
+/* One V(nu1, nu2) cycle of Algorithm 2 on u (in place). */
+int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int nu1, int nu2);
+/* ||f + d g - A_{h,tau} u||_inf into *out_max (host). */
+int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const double* g,
+                       double* out_max);
+/* V(nu1, nu2) cycles from the initial guess in u until ||r_k||_inf <= rtol ||r_0||_inf or
+ * max_cycles.  cycles_out / relres_out (host, may be NULL) receive the cycle count and
+ * ||r_k||/||r_0||.  With prec FHMG_MIXED_FP32 the cycles run in FP32 on the correction
+ * equation and the defect is recomputed in FP64 after each inner stage (defect correction);
+ * *cycles_out then counts inner cycles. */
+int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int nu1, int nu2,
+               double rtol, int max_cycles, int* cycles_out, double* relres_out);
+/* fhmg_solve with HOST arrays (u in/out, f, g or NULL): copies in, solves, copies u back. */
+int fhmg_solve_host(fhmg_problem p, double* u_host, const double* f_host, const double* g_host,
+                    int nu1, int nu2, double rtol, int max_cycles, int* cycles_out,
+                    double* relres_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHMG_H_ */

@@ -1,0 +1,214 @@
+"""Python binding of libfhmg (include/fhmg.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module checks tensor shapes/dtypes, passes
+``data_ptr()`` and the current CUDA stream, and turns status codes into exceptions.  It fails
+loudly (ImportError / RuntimeError) when the library has not been built -- there is no CPU
+fallback.
+
+Grid functions are torch.float64 CUDA tensors of shape (M, N) (1D) or (M, N, N) (2D),
+time-major with space contiguous, for t_1..t_M.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfhmg.so")
+
+FHMG_OK, FHMG_EINVAL, FHMG_ECUDA, FHMG_ENOMEM, FHMG_ENOTCONV, FHMG_ENAN, FHMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+FP64, MIXED_FP32 = 0, 1
+_STATUS = {0: "FHMG_OK", -1: "FHMG_EINVAL", -2: "FHMG_ECUDA", -3: "FHMG_ENOMEM", -4: "FHMG_ENOTCONV",
+           -5: "FHMG_ENAN", -6: "FHMG_ETIMEOUT"}
+
+_lib = None
+
+_c = ctypes
+_P = _c.c_void_p
+_D = _c.c_double
+_I = _c.c_int
+_LL = _c.c_longlong
+_SIGS = {
+    "fhmg_last_error": (_c.c_char_p, []),
+    "fhmg_build_hmatrix": (_I, [_D, _D, _D, _I, _I, _I, _D, _c.POINTER(_P)]),
+    "fhmg_hmatrix_info": (_I, [_P, _c.POINTER(_I), _c.POINTER(_I), _c.POINTER(_I), _c.POINTER(_c.c_size_t)]),
+    "fhmg_hmatrix_mesh": (_I, [_P, _P, _P]),
+    "fhmg_hmatrix_dense": (_I, [_P, _P]),
+    "fhmg_hmatrix_flops": (_I, [_P, _c.POINTER(_D)]),
+    "fhmg_hmatrix_destroy": (_I, [_P]),
+    "fhmg_problem_create": (_I, [_P, _I, _I, _D, _I, _P, _c.POINTER(_P)]),
+    "fhmg_problem_destroy": (_I, [_P]),
+    "fhmg_problem_autotune": (_I, [_P]),
+    "fhmg_problem_profile": (_I, [_P, _I]),
+    "fhmg_problem_counters": (_I, [_P, _c.POINTER(_LL), _c.POINTER(_LL), _c.POINTER(_D)]),
+    "fhmg_line_solve": (_I, [_P, _I, _P, _P, _LL]),
+    "fhmg_hmatvec": (_I, [_P, _P, _P, _LL]),
+    "fhmg_smooth": (_I, [_P, _P, _P, _I]),
+    "fhmg_residual": (_I, [_P, _P, _P, _P, _P]),
+    "fhmg_restrict_residual": (_I, [_P, _P, _P, _P]),
+    "fhmg_prolong_correct": (_I, [_P, _P, _P]),
+    "fhmg_vcycle": (_I, [_P, _P, _P, _P, _I, _I]),
+    "fhmg_residual_norm": (_I, [_P, _P, _P, _P, _c.POINTER(_D)]),
+    "fhmg_solve": (_I, [_P, _P, _P, _P, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
+    "fhmg_solve_host": (_I, [_P, _P, _P, _P, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
+}
+
+
+def lib():
+    """The loaded library (ctypes.CDLL); raises ImportError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfhmg.so not built ({LIB_PATH}); run paper_1706_07632_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class FhmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, allow=()):
+    if status != FHMG_OK and status not in allow:
+        raise FhmgError(status, lib().fhmg_last_error().decode())
+    return status
+
+
+def _ptr(x):
+    """Device (or host) pointer of a tensor/array, or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        import torch
+        if x.dtype != torch.float64:
+            raise TypeError("arrays must be float64")
+        return x.data_ptr()
+    return x.ctypes.data  # numpy (host) arrays for the *_host entry points
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class HMatrix:
+    """fhmg_build_hmatrix: mesh, L1 matrix and its H-matrix form (host, one-time)."""
+
+    def __init__(self, alpha, gamma, T, M, leaf=64, rank=0, tol=1e-10):
+        h = _P()
+        _check(lib().fhmg_build_hmatrix(alpha, gamma, T, M, leaf, rank, tol, ctypes.byref(h)))
+        self._h = h
+        self.alpha, self.gamma, self.T, self.M = alpha, gamma, T, M
+        self.leaf, self.rank, self.tol = leaf, rank, tol
+
+    def info(self):
+        nd, nr, mr, by = _I(), _I(), _I(), _c.c_size_t()
+        _check(lib().fhmg_hmatrix_info(self._h, ctypes.byref(nd), ctypes.byref(nr), ctypes.byref(mr), ctypes.byref(by)))
+        return {"n_dense": nd.value, "n_lowrank": nr.value, "max_rank": mr.value, "bytes": by.value}
+
+    def mesh(self):
+        import numpy as np
+        t = np.empty(self.M + 1)
+        d = np.empty(self.M)
+        _check(lib().fhmg_hmatrix_mesh(self._h, t.ctypes.data, d.ctypes.data))
+        return t, d
+
+    def dense(self):
+        import numpy as np
+        R = np.empty((self.M, self.M))
+        _check(lib().fhmg_hmatrix_dense(self._h, R.ctypes.data))
+        return R
+
+    def flops_per_column(self):
+        v = _D()
+        _check(lib().fhmg_hmatrix_flops(self._h, ctypes.byref(v)))
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fhmg_hmatrix_destroy(self._h)
+            self._h = None
+
+
+class Problem:
+    """fhmg_problem_create: a dim-D grid of N^dim interior points on the current CUDA device."""
+
+    def __init__(self, hm: HMatrix, dim, N, Lx=1.0, prec=FP64, stream=None):
+        p = _P()
+        _check(lib().fhmg_problem_create(hm._h, dim, N, Lx, prec, _stream_ptr(stream), ctypes.byref(p)))
+        self._p = p
+        self.hm, self.dim, self.N, self.Lx, self.prec = hm, dim, N, Lx, prec
+        self.M = hm.M
+        self.levels = (N + 1).bit_length() - 1
+
+    def shape(self, N=None):
+        N = self.N if N is None else N
+        return (self.M, N) if self.dim == 1 else (self.M, N, N)
+
+    def autotune(self):
+        _check(lib().fhmg_problem_autotune(self._p))
+
+    def profile(self, enable=True):
+        _check(lib().fhmg_problem_profile(self._p, 1 if enable else 0))
+
+    def counters(self):
+        n, ns, ms = _LL(), _LL(), _D()
+        _check(lib().fhmg_problem_counters(self._p, ctypes.byref(n), ctypes.byref(ns), ctypes.byref(ms)))
+        return {"launches": n.value, "smooth_launches": ns.value, "smooth_ms": ms.value}
+
+    def line_solve(self, level, X, B):
+        ncols = B.numel() // self.M
+        _check(lib().fhmg_line_solve(self._p, level, _ptr(X), _ptr(B), ncols))
+
+    def hmatvec(self, Y, X):
+        _check(lib().fhmg_hmatvec(self._p, _ptr(Y), _ptr(X), X.numel() // self.M))
+
+    def smooth(self, u, F, nsweeps=1):
+        _check(lib().fhmg_smooth(self._p, _ptr(u), _ptr(F), nsweeps))
+
+    def residual(self, u, f, g, r):
+        _check(lib().fhmg_residual(self._p, _ptr(u), _ptr(f), _ptr(g), _ptr(r)))
+
+    def restrict_residual(self, u, F, rc):
+        _check(lib().fhmg_restrict_residual(self._p, _ptr(u), _ptr(F), _ptr(rc)))
+
+    def prolong_correct(self, u, e):
+        _check(lib().fhmg_prolong_correct(self._p, _ptr(u), _ptr(e)))
+
+    def vcycle(self, u, f, g=None, nu1=1, nu2=1):
+        _check(lib().fhmg_vcycle(self._p, _ptr(u), _ptr(f), _ptr(g), nu1, nu2))
+
+    def residual_norm(self, u, f, g=None):
+        v = _D()
+        _check(lib().fhmg_residual_norm(self._p, _ptr(u), _ptr(f), _ptr(g), ctypes.byref(v)))
+        return v.value
+
+    def solve(self, u, f, g=None, nu1=1, nu2=1, rtol=1e-10, max_cycles=50, allow_notconv=False):
+        k, rr = _I(), _D()
+        st = lib().fhmg_solve(self._p, _ptr(u), _ptr(f), _ptr(g), nu1, nu2, rtol, max_cycles,
+                              ctypes.byref(k), ctypes.byref(rr))
+        _check(st, allow=(FHMG_ENOTCONV,) if allow_notconv else ())
+        return k.value, rr.value
+
+    def solve_host(self, u, f, g=None, nu1=1, nu2=1, rtol=1e-10, max_cycles=50):
+        """u, f, g: C-contiguous float64 host arrays (numpy or pinned CPU tensors)."""
+        k, rr = _I(), _D()
+        _check(lib().fhmg_solve_host(self._p, _ptr(u), _ptr(f), _ptr(g), nu1, nu2, rtol, max_cycles,
+                                     ctypes.byref(k), ctypes.byref(rr)))
+        return k.value, rr.value
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _lib is not None:
+            _lib.fhmg_problem_destroy(self._p)
+            self._p = None

@@ -1,0 +1,79 @@
+// Host-side construction of the H-matrix approximation of the L1 time matrix R.
+//
+// Section 2 defines R (Eq. elements_matrix_R) on the graded mesh t_m = T (m/M)^gamma;
+// Section 3 builds its H-matrix form: index bisection of {1..M}, the admissibility condition
+// of Definition 3.1, Taylor degenerate-kernel factors (Eqs. A_elements, B_elements).  On top
+// of the paper's construction this builder recompresses each Taylor block (Householder QR of
+// both factors + SVD of the small core) to a block-relative tolerance, and flattens the
+// block tree into per-leaf-row panels that the CUDA kernels walk in time order.
+#pragma once
+#include <cstddef>
+#include <vector>
+
+namespace fhmg {
+
+struct RkBlock {
+  int r0, r1, c0, c1;   // rows r0..r1-1, columns c0..c1-1 (0-based: row m = r0+1, ...)
+  int k;                // rank
+  std::vector<double> U;  // (r1-r0) x k, row-major
+  std::vector<double> V;  // (c1-c0) x k, row-major;  block = U V^T
+};
+
+struct DenseBlock {
+  int bi, bj;               // leaf-row / leaf-column index
+  std::vector<double> D;    // L x L row-major
+};
+
+struct HostH {
+  double alpha = 0, gamma = 0, T = 0;
+  int M = 0, L = 0, nb = 0;
+  int rank = 0;             // > 0: fixed Taylor terms, no recompression
+  double tol = 0;           // > 0: recompression tolerance (block-relative)
+  bool dense_mode = false;  // rank == 0 && tol == 0: every lower block dense
+  std::vector<double> t;    // mesh, M+1
+  std::vector<double> dmm;  // initial-data weights d_{m,m}, M
+  std::vector<DenseBlock> dense;  // includes the diagonal blocks
+  std::vector<int> diag;          // per leaf row: index into dense
+  std::vector<RkBlock> rk;
+  int max_rank = 0;
+  int taylor_terms = 0;
+};
+
+// Flattened, leaf-row ordered form used by the kernels (all offsets in elements).
+struct FlatH {
+  int M, L, nb;
+  int pool_rows;                    // z-pool rows needed (max live sum of ranks)
+  // dense off-diagonal blocks per leaf row (j < i), then diagonal handled separately
+  std::vector<int> dptr;            // nb+1: range into dlist
+  std::vector<int> dlist_blk;       // index into dense block storage
+  std::vector<int> dlist_col;       // leaf-column index j
+  std::vector<double> dense_data;   // nd x L x L
+  std::vector<int> diag_blk;        // nb: block index of the diagonal block
+  // U panels: leaf row i uses rows iL..iL+L-1 of every Rk block covering it
+  std::vector<int> uptr;            // nb+1: range of panel columns (z rows) per leaf row
+  std::vector<int> uz;              // z-pool row of each panel column
+  std::vector<long long> uoff;      // nb: element offset of the L x K_i panel (row-major)
+  std::vector<double> udata;
+  // V panels: leaf row i contributes V^T x_i to every Rk block whose columns cover it
+  std::vector<int> vptr;            // nb+1
+  std::vector<int> vz;              // z-pool row written by each panel row
+  std::vector<int> vinit;           // 1: first leaf of the block's columns (assign, not add)
+  std::vector<long long> voff;      // nb: element offset of the K'_i x L panel (row-major)
+  std::vector<double> vdata;
+  long long flops_per_col_matvec;   // 2 * (stored lower entries touched) per column, matvec
+  long long flops_per_col_solve;
+};
+
+// Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
+// Returns 0 on success, < 0 on invalid arguments.
+int build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,
+                  HostH& out);
+void flatten(const HostH& h, FlatH& f);
+
+// Accurate single entry R_{m,j} (1-based, 1 <= j <= m), used for dense blocks.
+double l1_entry(const std::vector<double>& t, double alpha, int m, int j);
+
+// (D_ii + s I)^{-1} for every diagonal leaf block (lower-triangular L x L, row-major).
+void diag_inverses(const HostH& h, const FlatH& f, double shift, std::vector<double>& out);
+
+}  // namespace fhmg

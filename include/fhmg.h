@@ -87,6 +87,9 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
 int fhmg_problem_destroy(fhmg_problem p);
 /* Chooses the column tile of each kernel by timing (autotuner); optional. */
 int fhmg_problem_autotune(fhmg_problem p);
+/* Mixed path: V-cycles run on the correction equation between two FP64 defect evaluations
+ * (default 3, >= 1). */
+int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles);
 /* Resets the counters below and, if enable != 0, records CUDA events on the problem's stream
  * around every smoother launch on the finest grid (the dominant kernel). */
 int fhmg_problem_profile(fhmg_problem p, int enable);

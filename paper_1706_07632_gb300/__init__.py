@@ -40,6 +40,7 @@ _SIGS = {
     "fhmg_problem_destroy": (_I, [_P]),
     "fhmg_problem_autotune": (_I, [_P]),
     "fhmg_problem_profile": (_I, [_P, _I]),
+    "fhmg_problem_set_inner": (_I, [_P, _I]),
     "fhmg_problem_counters": (_I, [_P, _c.POINTER(_LL), _c.POINTER(_LL), _c.POINTER(_D)]),
     "fhmg_line_solve": (_I, [_P, _I, _P, _P, _LL]),
     "fhmg_hmatvec": (_I, [_P, _P, _P, _LL]),
@@ -158,6 +159,9 @@ class Problem:
 
     def autotune(self):
         _check(lib().fhmg_problem_autotune(self._p))
+
+    def set_inner(self, cycles):
+        _check(lib().fhmg_problem_set_inner(self._p, cycles))
 
     def profile(self, enable=True):
         _check(lib().fhmg_problem_profile(self._p, 1 if enable else 0))

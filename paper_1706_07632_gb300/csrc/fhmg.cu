@@ -12,9 +12,9 @@
 #include "fhmg.h"
 #include "hbuild.h"
 #include "kernels.cuh"
+#include "walk.h"
 
 using fhmg::Geo;
-using fhmg::HDev;
 
 namespace {
 
@@ -30,10 +30,10 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-#define CK(x)                                                                         \
-  do {                                                                                \
-    cudaError_t e_ = (x);                                                             \
-    if (e_ != cudaSuccess) return fail(FHMG_ECUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess) return fail(FHMG_ECUDA, "%s: %s", #x, cudaGetErrorString(e_));       \
   } while (0)
 #define TRY(...)                    \
   do {                              \
@@ -52,10 +52,9 @@ struct fhmg_hmatrix_s {
 
 namespace {
 
-template <typename T>
-struct DevH {
+struct DevPanel {
   std::vector<void*> allocs;
-  HDev<T> d{};
+  fhmg::PanelDev d{};
   size_t bytes = 0;
 };
 
@@ -63,12 +62,11 @@ struct LevelData {
   int N = 0;
   long long npts = 0;
   double h = 0, inv_h2 = 0, shift = 0;
-  double* E = nullptr;   // unknown of the coarse-grid correction (coarse levels)
-  double* RC = nullptr;  // restricted defect (coarse levels)
-  double* Dinv64 = nullptr;
-  float* Dinv32 = nullptr;
-  int tc_smooth[2] = {0, 0};
-  int tc_matvec = 0;
+  double* E = nullptr;         // unknown of the coarse-grid correction (coarse levels)
+  double* RC = nullptr;        // restricted defect (coarse levels)
+  double* Dinv64 = nullptr;    // (D_ii + s I)^{-1}, FP64, column-major
+  float* Dinv32 = nullptr;     // the same in FP32 (mixed path; its diagonal is not used)
+  double* dinvdiag = nullptr;  // FP64 diagonal of the inverses (mixed path)
 };
 
 }  // namespace
@@ -79,21 +77,25 @@ struct fhmg_problem_s {
   double Lx = 1.0;
   cudaStream_t st = nullptr;
   int M = 0, L = 0, nb = 0;
-  DevH<double> h64;
-  DevH<float> h32;
+  DevPanel panel64;  // chunk stream, FP64 matrices
+  DevPanel panel32;  // chunk stream, FP32 matrices (mixed path)
+  double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path)
   std::vector<LevelData> lev;
   double* Xs = nullptr;  // scratch, >= max(colour-0 count, coarse count) * M
-  double* Rs = nullptr;  // scratch, fine points * M
+  double* Rs = nullptr;  // scratch, fine points * M (defect)
+  double* Ef = nullptr;  // fine-grid correction of the mixed path
   double* Ff = nullptr;  // f + d g when g is given
   double* dmm = nullptr; // d_{m,m}
   unsigned long long* dnorm = nullptr;
+  int* derr = nullptr;   // device error word of the panel kernels (bounded-wait timeout)
   double* hu = nullptr;  // device copies for fhmg_solve_host
   double* hf = nullptr;
   double* hg = nullptr;
+  int inner = 3;         // inner V-cycles per defect-correction step (mixed path)
   std::vector<void*> allocs;
-  long long launches = 0;                 // kernel launches issued (all kernels)
-  bool profile = false;                   // record events around finest-level smoother walks
-  std::vector<cudaEvent_t> ev;            // start/stop pairs
+  long long launches = 0;       // kernel launches issued (all kernels)
+  bool profile = false;         // record events around finest-level smoother walks
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
   size_t ev_used = 0;
 };
 
@@ -119,93 +121,32 @@ int upload(std::vector<void*>& list, const std::vector<S>& src, const T** out, s
   return FHMG_OK;
 }
 
-// row-major -> column-major for a stack of rows x cols blocks
+// row-major -> column-major for a rows x cols block
 void transpose_into(const double* in, double* out, int rows, int cols) {
   for (int r = 0; r < rows; ++r)
     for (int c = 0; c < cols; ++c) out[(size_t)c * rows + r] = in[(size_t)r * cols + c];
 }
 
-template <typename T>
-int upload_h(const fhmg::FlatH& f, DevH<T>& D) {
-  const int L = f.L, nb = f.nb;
-  std::vector<double> dense(f.dense_data.size()), ud(f.udata.size()), vd(f.vdata.size());
-  size_t nd = f.dense_data.size() / ((size_t)L * L);
-  for (size_t b = 0; b < nd; ++b)
-    transpose_into(&f.dense_data[b * L * L], &dense[b * L * L], L, L);
-  for (int i = 0; i < nb; ++i) {
-    int K = f.uptr[i + 1] - f.uptr[i];
-    if (K) transpose_into(&f.udata[f.uoff[i]], &ud[f.uoff[i]], L, K);
-    int Kv = f.vptr[i + 1] - f.vptr[i];
-    if (Kv) transpose_into(&f.vdata[f.voff[i]], &vd[f.voff[i]], Kv, L);
-  }
-  HDev<T>& d = D.d;
-  TRY(upload(D.allocs, dense, &d.dense, &D.bytes));
-  TRY(upload(D.allocs, f.dptr, &d.dptr, &D.bytes));
-  TRY(upload(D.allocs, f.dlist_blk, &d.dblk, &D.bytes));
-  TRY(upload(D.allocs, f.dlist_col, &d.dcol, &D.bytes));
-  TRY(upload(D.allocs, f.diag_blk, &d.diag, &D.bytes));
-  TRY(upload(D.allocs, f.uptr, &d.uptr, &D.bytes));
-  TRY(upload(D.allocs, f.uz, &d.uz, &D.bytes));
-  TRY(upload(D.allocs, f.uoff, &d.uoff, &D.bytes));
-  TRY(upload(D.allocs, ud, &d.udata, &D.bytes));
-  TRY(upload(D.allocs, f.vptr, &d.vptr, &D.bytes));
-  TRY(upload(D.allocs, f.vz, &d.vz, &D.bytes));
-  TRY(upload(D.allocs, f.vinit, &d.vinit, &D.bytes));
-  TRY(upload(D.allocs, f.voff, &d.voff, &D.bytes));
-  TRY(upload(D.allocs, vd, &d.vdata, &D.bytes));
-  d.M = f.M;
-  d.L = L;
-  d.nb = nb;
-  d.pool = f.pool_rows;
+// Uploads the chunk stream of the H-matrix (elem_bytes 8: FP64 products, 4: FP32 products).
+int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, DevPanel& D) {
+  fhmg::PanelHost ph;
+  fhmg::build_panel(h, f, elem_bytes, ph);
+  const unsigned char* pkg;
+  const int* chunks;
+  const int* cptr;
+  TRY(upload(D.allocs, ph.pkg, &pkg, &D.bytes));
+  TRY(upload(D.allocs, ph.chunks, &chunks, &D.bytes));
+  TRY(upload(D.allocs, ph.cptr, &cptr, &D.bytes));
+  D.d.pkg = pkg;
+  D.d.chunks = reinterpret_cast<const int4*>(chunks);
+  D.d.cptr = cptr;
+  D.d.nb = f.nb;
+  D.d.L = f.L;
+  D.d.pool = f.pool_rows;
+  D.d.W = ph.W;
+  D.d.slot_bytes = ph.slot_bytes;
+  D.d.ns = 2;
   return FHMG_OK;
-}
-
-template <typename T>
-size_t walk_smem(int L, int TC, int pool) {
-  return (size_t)(L * TC + pool * TC) * sizeof(T);
-}
-
-template <typename T, int L, int TC, int MODE>
-int launch_walk_t(cudaStream_t st, const HDev<T>& H, const Geo& geo, long long ncols, T* X, const T* B,
-                  T* OUT, const T* Dinv, unsigned long long* norm) {
-  auto kern = fhmg::hwalk_kernel<T, L, TC, MODE>;
-  const size_t smem = walk_smem<T>(L, TC, H.pool);
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
-  const long long grid = (ncols + TC - 1) / TC;
-  if (grid <= 0) return FHMG_OK;
-  if (grid > 0x7fffffffLL) return fail(FHMG_EINVAL, "too many columns");
-  kern<<<(unsigned)grid, fhmg::Tile<L, TC>::NT, smem, st>>>(H, geo, ncols, X, B, OUT, Dinv, norm);
-  CK(cudaGetLastError());
-  return FHMG_OK;
-}
-
-template <typename T, int MODE>
-int launch_walk(fhmg_problem p, const HDev<T>& H, int TC, const Geo& geo, long long ncols, T* X, const T* B,
-                T* OUT, const T* Dinv, unsigned long long* norm) {
-  cudaStream_t st = p->st;
-  if (ncols > 0) ++p->launches;
-#define FHMG_CASE(LL, TT)                                                                  \
-  if (H.L == LL && TC == TT) return launch_walk_t<T, LL, TT, MODE>(st, H, geo, ncols, X, B, OUT, Dinv, norm);
-  FHMG_CASE(16, 1) FHMG_CASE(16, 2) FHMG_CASE(16, 4) FHMG_CASE(16, 8) FHMG_CASE(16, 16)
-  FHMG_CASE(32, 1) FHMG_CASE(32, 2) FHMG_CASE(32, 4) FHMG_CASE(32, 8) FHMG_CASE(32, 16)
-  FHMG_CASE(64, 1) FHMG_CASE(64, 2) FHMG_CASE(64, 4) FHMG_CASE(64, 8) FHMG_CASE(64, 16)
-#undef FHMG_CASE
-  return fail(FHMG_EINVAL, "no kernel for leaf %d and column tile %d", H.L, TC);
-}
-
-// Column tile: the smallest of 1..16 whose grid fits in about one wave of 7 resident 256-thread
-// CTAs per SM (more CTAs than that only adds waves; fewer columns per CTA keeps each CTA's
-// sequential leaf chain short), shrunk if the z-pool does not fit in shared memory.
-template <typename T>
-int pick_tc(const HDev<T>& H, long long ncols) {
-  int tc = 1;
-  while (tc < 16 && (ncols + tc - 1) / tc > 7LL * kSMs) tc *= 2;
-  while (tc > 1 && walk_smem<T>(H.L, tc, H.pool) > 200 * 1024) tc /= 2;
-  return tc;
 }
 
 int blocks_for(long long n) {
@@ -228,34 +169,82 @@ int record_event(fhmg_problem p) {
   return FHMG_OK;
 }
 
-// ---------------------------------------------------------------- driver steps (FP64)
+int walk_status(int s, const std::string& err) {
+  if (s == 0) return FHMG_OK;
+  return fail(s == 1 ? FHMG_ECUDA : FHMG_EINVAL, "%s", err.c_str());
+}
 
-int sweep(fhmg_problem p, int l, double* u, const double* F) {
+int walk(fhmg_problem p, bool mixed, fhmg::WalkArgs& a) {
+  if (a.ncols <= 0) return FHMG_OK;
+  std::string err;
+  ++p->launches;
+  a.err = p->derr;
+  a.tile = 0;
+  if (mixed) {
+    a.P = p->panel32.d;
+    return walk_status(fhmg::walk_launch_df(p->st, a, &err, nullptr), err);
+  }
+  a.P = p->panel64.d;
+  return walk_status(fhmg::walk_launch_dd(p->st, a, &err, nullptr), err);
+}
+
+// One smoother half-sweep / line solve walk on level l (shift of that level).
+int walk_smooth(fhmg_problem p, int l, bool mixed, const Geo& g, long long nc, double* X, const double* B) {
+  LevelData& lv = p->lev[l];
+  fhmg::WalkArgs a{};
+  a.mode = fhmg::MODE_SMOOTH;
+  a.geo = g;
+  a.ncols = nc;
+  a.X = X;
+  a.B = B;
+  a.OUT = nullptr;
+  a.Dinv = mixed ? (const void*)lv.Dinv32 : (const void*)lv.Dinv64;
+  a.ddiag = mixed ? lv.dinvdiag : nullptr;
+  a.norm = nullptr;
+  return walk(p, mixed, a);
+}
+
+// OUT = B - R~ X on nc compact columns (OUT may alias B or be NULL); optional max-norm.
+int walk_matvec(fhmg_problem p, bool mixed, long long nc, const double* X, const double* B, double* OUT,
+                unsigned long long* norm) {
+  fhmg::WalkArgs a{};
+  a.mode = fhmg::MODE_MATVEC;
+  a.geo = Geo{0, 0, 0, nc, 0.0};
+  a.ncols = nc;
+  a.X = const_cast<double*>(X);
+  a.B = B;
+  a.OUT = OUT;
+  a.Dinv = nullptr;
+  a.ddiag = mixed ? p->rdiag : nullptr;
+  a.norm = norm;
+  return walk(p, mixed, a);
+}
+
+// ---------------------------------------------------------------- driver steps
+
+int sweep(fhmg_problem p, int l, double* u, const double* F, bool mixed) {
   LevelData& lv = p->lev[l];
   for (int colour = 0; colour < 2; ++colour) {
     const long long nc = fhmg::colour_count(p->dim, lv.N, colour);
     if (nc == 0) continue;
     Geo g{p->dim, lv.N, colour, lv.npts, lv.inv_h2};
-    int tc = lv.tc_smooth[colour] ? lv.tc_smooth[colour] : pick_tc(p->h64.d, nc);
     const bool rec = p->profile && l == p->nlev - 1;
     if (rec) TRY(record_event(p));
-    TRY(launch_walk<double, fhmg::MODE_SMOOTH>(p, p->h64.d, tc, g, nc, u, F, nullptr, lv.Dinv64, nullptr));
+    TRY(walk_smooth(p, l, mixed, g, nc, u, F));
     if (rec) TRY(record_event(p));
   }
   return FHMG_OK;
 }
 
 // rc = FW(F - A_h u) - R~ FW(u) on level l-1
-int restrict_defect(fhmg_problem p, int l, const double* u, const double* F, double* rc) {
+int restrict_defect(fhmg_problem p, int l, const double* u, const double* F, double* rc, bool mixed) {
   LevelData& lv = p->lev[l];
   LevelData& lc = p->lev[l - 1];
   const long long n = lc.npts * p->M;
   fhmg::restrict_pre_kernel<double><<<blocks_for(n), 256, 0, p->st>>>(p->dim, lv.N, lv.inv_h2, p->M, u, F, p->Xs, rc);
   ++p->launches;
   CK(cudaGetLastError());
-  Geo g{0, 0, 0, lc.npts, 0.0};
-  int tc = lc.tc_matvec ? lc.tc_matvec : pick_tc(p->h64.d, lc.npts);
-  return launch_walk<double, fhmg::MODE_MATVEC>(p, p->h64.d, tc, g, lc.npts, p->Xs, rc, rc, nullptr, nullptr);
+  return walk_matvec(p, mixed, lc.npts, p->Xs, rc, rc, nullptr);
 }
 
 int prolong_add(fhmg_problem p, int l, const double* e, double* u) {
@@ -266,21 +255,35 @@ int prolong_add(fhmg_problem p, int l, const double* e, double* u) {
   return FHMG_OK;
 }
 
-int vcycle_rec(fhmg_problem p, int l, double* u, const double* F, int nu1, int nu2) {
-  if (l == 0) return sweep(p, 0, u, F);  // one interior point: the colour-0 solve is exact
-  for (int s = 0; s < nu1; ++s) TRY(sweep(p, l, u, F));
+int vcycle_rec(fhmg_problem p, int l, double* u, const double* F, int nu1, int nu2, bool mixed) {
+  if (l == 0) return sweep(p, 0, u, F, mixed);  // one interior point: the colour-0 solve is exact
+  for (int s = 0; s < nu1; ++s) TRY(sweep(p, l, u, F, mixed));
   LevelData& lc = p->lev[l - 1];
-  TRY(restrict_defect(p, l, u, F, lc.RC));
+  TRY(restrict_defect(p, l, u, F, lc.RC, mixed));
   CK(cudaMemsetAsync(lc.E, 0, sizeof(double) * lc.npts * p->M, p->st));
-  TRY(vcycle_rec(p, l - 1, lc.E, lc.RC, nu1, nu2));
+  TRY(vcycle_rec(p, l - 1, lc.E, lc.RC, nu1, nu2, mixed));
   TRY(prolong_add(p, l, lc.E, u));
-  for (int s = 0; s < nu2; ++s) TRY(sweep(p, l, u, F));
+  for (int s = 0; s < nu2; ++s) TRY(sweep(p, l, u, F, mixed));
   return FHMG_OK;
 }
 
-// max |F - A_{h,tau} u| on the finest grid; colour0_only after a completed red-black sweep
-// (the defect then vanishes on colour 1 up to rounding).
-int fine_norm(fhmg_problem p, const double* u, const double* F, bool colour0_only, double* out) {
+int read_norm(fhmg_problem p, double* out) {
+  unsigned long long bits = 0;
+  int derr = 0;
+  CK(cudaMemcpyAsync(&bits, p->dnorm, sizeof bits, cudaMemcpyDeviceToHost, p->st));
+  CK(cudaMemcpyAsync(&derr, p->derr, sizeof derr, cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  if (derr) return fail(FHMG_ETIMEOUT, "a panel kernel gave up waiting on a shared-memory stage");
+  double v;
+  std::memcpy(&v, &bits, sizeof v);
+  *out = v;
+  return FHMG_OK;
+}
+
+// FP64 defect on the finest grid.  colour0_only (after a completed red-black sweep the defect
+// vanishes on colour 1 up to rounding): max-norm over colour 0 only, nothing stored.
+// Otherwise the full defect is written to R (if R != NULL) and its max-norm returned.
+int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_only, double* R, double* out) {
   LevelData& lv = p->lev[p->nlev - 1];
   CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), p->st));
   if (colour0_only && lv.npts > 1) {
@@ -289,25 +292,16 @@ int fine_norm(fhmg_problem p, const double* u, const double* F, bool colour0_onl
                                                                                   p->Xs, p->Rs);
     ++p->launches;
     CK(cudaGetLastError());
-    Geo g{0, 0, 0, nc, 0.0};
-    TRY(launch_walk<double, fhmg::MODE_MATVEC>(p, p->h64.d, pick_tc(p->h64.d, nc), g, nc, p->Xs, p->Rs, nullptr,
-                                               nullptr, p->dnorm));
+    TRY(walk_matvec(p, false, nc, p->Xs, p->Rs, nullptr, p->dnorm));
   } else {
+    double* dst = R ? R : p->Rs;
     fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
-                                                                                       u, F, nullptr, p->Rs);
+                                                                                       u, F, nullptr, dst);
     ++p->launches;
     CK(cudaGetLastError());
-    Geo g{0, 0, 0, lv.npts, 0.0};
-    TRY(launch_walk<double, fhmg::MODE_MATVEC>(p, p->h64.d, pick_tc(p->h64.d, lv.npts), g, lv.npts,
-                                               const_cast<double*>(u), p->Rs, nullptr, nullptr, p->dnorm));
+    TRY(walk_matvec(p, false, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
   }
-  unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(&bits, p->dnorm, sizeof bits, cudaMemcpyDeviceToHost, p->st));
-  CK(cudaStreamSynchronize(p->st));
-  double v;
-  std::memcpy(&v, &bits, sizeof v);
-  *out = v;
-  return FHMG_OK;
+  return read_norm(p, out);
 }
 
 // F = f + d g into the problem's buffer (or f itself when g is NULL)
@@ -323,6 +317,62 @@ int full_rhs(fhmg_problem p, const double* f, const double* g, const double** F)
   ++p->launches;
   CK(cudaGetLastError());
   *F = p->Ff;
+  return FHMG_OK;
+}
+
+__global__ void axpy_kernel(double* y, const double* x, long long n, double a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+int axpy(fhmg_problem p, double* y, const double* x, long long n, double a) {
+  axpy_kernel<<<blocks_for(n), 256, 0, p->st>>>(y, x, n, a);
+  ++p->launches;
+  CK(cudaGetLastError());
+  return FHMG_OK;
+}
+
+// FP64 path: V-cycles on u until the colour-0 defect norm is below rtol * ||r_0||.
+int solve_fp64(fhmg_problem p, double* u, const double* F, int nu1, int nu2, double rtol, int max_cycles, int* kout,
+               double* r0out, double* rout) {
+  double r0, r;
+  TRY(fine_defect(p, u, F, false, nullptr, &r0));
+  if (!std::isfinite(r0)) return fail(FHMG_ENAN, "initial residual is not finite");
+  r = r0;
+  int k = 0;
+  while (r > rtol * r0 && k < max_cycles) {
+    TRY(vcycle_rec(p, p->nlev - 1, u, F, nu1, nu2, false));
+    TRY(fine_defect(p, u, F, nu2 > 0, nullptr, &r));
+    ++k;
+    if (!std::isfinite(r)) return fail(FHMG_ENAN, "residual became non-finite after %d cycles", k);
+  }
+  *kout = k;
+  *r0out = r0;
+  *rout = r;
+  return FHMG_OK;
+}
+
+// Mixed path (defect correction): r = F - A u in FP64; p->inner V-cycles with FP32 H-matrix
+// products on A e = r from e = 0; u += e; repeat until ||r|| <= rtol ||r_0||.
+int solve_mixed(fhmg_problem p, double* u, const double* F, int nu1, int nu2, double rtol, int max_cycles, int* kout,
+                double* r0out, double* rout) {
+  const long long n = p->lev[p->nlev - 1].npts * p->M;
+  double r0, r;
+  TRY(fine_defect(p, u, F, false, p->Rs, &r0));
+  if (!std::isfinite(r0)) return fail(FHMG_ENAN, "initial residual is not finite");
+  r = r0;
+  int k = 0;
+  while (r > rtol * r0 && k < max_cycles) {
+    CK(cudaMemsetAsync(p->Ef, 0, sizeof(double) * n, p->st));
+    for (int j = 0; j < p->inner && k < max_cycles; ++j, ++k)
+      TRY(vcycle_rec(p, p->nlev - 1, p->Ef, p->Rs, nu1, nu2, true));
+    TRY(axpy(p, u, p->Ef, n, 1.0));
+    TRY(fine_defect(p, u, F, false, p->Rs, &r));
+    if (!std::isfinite(r)) return fail(FHMG_ENAN, "residual became non-finite after %d cycles", k);
+  }
+  *kout = k;
+  *r0out = r0;
+  *rout = r;
   return FHMG_OK;
 }
 
@@ -407,8 +457,8 @@ int fhmg_problem_destroy(fhmg_problem p) {
   if (!p) return FHMG_OK;
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
-  for (void* a : p->h64.allocs) cudaFree(a);
-  for (void* a : p->h32.allocs) cudaFree(a);
+  for (void* a : p->panel64.allocs) cudaFree(a);
+  for (void* a : p->panel32.allocs) cudaFree(a);
   delete p;
   return FHMG_OK;
 }
@@ -439,8 +489,17 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     fhmg_problem_destroy(p);
     return s;
   };
-  if ((st = upload_h(h->flat, p->h64)) != FHMG_OK) return bail(st);
-  if (prec == FHMG_MIXED_FP32 && (st = upload_h(h->flat, p->h32)) != FHMG_OK) return bail(st);
+  const bool mixed = prec == FHMG_MIXED_FP32;
+  if ((st = upload_panel(h->host, h->flat, 8, p->panel64)) != FHMG_OK) return bail(st);
+  if (mixed) {
+    if ((st = upload_panel(h->host, h->flat, 4, p->panel32)) != FHMG_OK) return bail(st);
+    std::vector<double> rd((size_t)p->nb * p->L);
+    for (int i = 0; i < p->nb; ++i)
+      for (int r = 0; r < p->L; ++r) rd[(size_t)i * p->L + r] = h->host.dense[h->host.diag[i]].D[(size_t)r * p->L + r];
+    const double* d;
+    if ((st = upload(p->allocs, rd, &d, nullptr)) != FHMG_OK) return bail(st);
+    p->rdiag = const_cast<double*>(d);
+  }
   const int M = p->M;
   for (int l = 0; l < nlev; ++l) {
     LevelData& lv = p->lev[l];
@@ -452,14 +511,21 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     std::vector<double> inv;
     fhmg::diag_inverses(h->host, h->flat, lv.shift, inv);
     std::vector<double> invT(inv.size());
-    for (int i = 0; i < p->nb; ++i) transpose_into(&inv[(size_t)i * p->L * p->L], &invT[(size_t)i * p->L * p->L], p->L, p->L);
+    for (int i = 0; i < p->nb; ++i)
+      transpose_into(&inv[(size_t)i * p->L * p->L], &invT[(size_t)i * p->L * p->L], p->L, p->L);
     const double* d64;
     if ((st = upload(p->allocs, invT, &d64, nullptr)) != FHMG_OK) return bail(st);
     lv.Dinv64 = const_cast<double*>(d64);
-    if (prec == FHMG_MIXED_FP32) {
+    if (mixed) {
       const float* d32;
       if ((st = upload(p->allocs, invT, &d32, nullptr)) != FHMG_OK) return bail(st);
       lv.Dinv32 = const_cast<float*>(d32);
+      std::vector<double> dg((size_t)p->nb * p->L);
+      for (int i = 0; i < p->nb; ++i)
+        for (int r = 0; r < p->L; ++r) dg[(size_t)i * p->L + r] = inv[(size_t)i * p->L * p->L + (size_t)r * p->L + r];
+      const double* dd;
+      if ((st = upload(p->allocs, dg, &dd, nullptr)) != FHMG_OK) return bail(st);
+      lv.dinvdiag = const_cast<double*>(dd);
     }
     if (l < nlev - 1) {
       if ((st = dalloc(p->allocs, &lv.E, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);
@@ -471,16 +537,25 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   long long coarse = nlev > 1 ? p->lev[nlev - 2].npts : 1;
   if ((st = dalloc(p->allocs, &p->Xs, (size_t)std::max(c0, coarse) * M)) != FHMG_OK) return bail(st);
   if ((st = dalloc(p->allocs, &p->Rs, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
+  if (mixed && (st = dalloc(p->allocs, &p->Ef, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
   const double* dm;
   if ((st = upload(p->allocs, h->host.dmm, &dm, nullptr)) != FHMG_OK) return bail(st);
   p->dmm = const_cast<double*>(dm);
   if ((st = dalloc(p->allocs, &p->dnorm, 1)) != FHMG_OK) return bail(st);
-  if (walk_smem<double>(p->L, 1, p->h64.d.pool) > 200 * 1024) return bail(fail(FHMG_EINVAL, "H-matrix z-pool too large"));
+  if ((st = dalloc(p->allocs, &p->derr, 1)) != FHMG_OK) return bail(st);
+  if (cudaMemset(p->derr, 0, sizeof(int)) != cudaSuccess) return bail(fail(FHMG_ECUDA, "cudaMemset failed"));
   *out = p;
   return FHMG_OK;
 }
 
 int fhmg_problem_autotune(fhmg_problem p) { return check_dims(p); }
+
+int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles) {
+  TRY(check_dims(p));
+  if (inner_cycles < 1) return fail(FHMG_EINVAL, "inner_cycles must be >= 1");
+  p->inner = inner_cycles;
+  return FHMG_OK;
+}
 
 int fhmg_problem_profile(fhmg_problem p, int enable) {
   TRY(check_dims(p));
@@ -511,17 +586,14 @@ int fhmg_line_solve(fhmg_problem p, int level, double* X, const double* B, long 
   if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
   if (!X || !B || ncols < 0) return fail(FHMG_EINVAL, "bad arrays");
   Geo g{0, 0, 0, ncols, 0.0};
-  return launch_walk<double, fhmg::MODE_SMOOTH>(p, p->h64.d, pick_tc(p->h64.d, ncols), g, ncols, X, B, nullptr,
-                                                p->lev[level].Dinv64, nullptr);
+  return walk_smooth(p, level, false, g, ncols, X, B);
 }
 
 int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
   TRY(check_dims(p));
   if (!X || !Y || ncols < 0 || X == Y) return fail(FHMG_EINVAL, "bad arrays");
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
-  Geo g{0, 0, 0, ncols, 0.0};
-  TRY(launch_walk<double, fhmg::MODE_MATVEC>(p, p->h64.d, pick_tc(p->h64.d, ncols), g, ncols,
-                                             const_cast<double*>(X), Y, Y, nullptr, nullptr));
+  TRY(walk_matvec(p, false, ncols, X, Y, Y, nullptr));
   scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
   ++p->launches;
   CK(cudaGetLastError());
@@ -531,7 +603,7 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
 int fhmg_smooth(fhmg_problem p, double* u, const double* F, int nsweeps) {
   TRY(check_dims(p));
   if (!u || !F || nsweeps < 0) return fail(FHMG_EINVAL, "bad arguments");
-  for (int s = 0; s < nsweeps; ++s) TRY(sweep(p, p->nlev - 1, u, F));
+  for (int s = 0; s < nsweeps; ++s) TRY(sweep(p, p->nlev - 1, u, F, false));
   return FHMG_OK;
 }
 
@@ -540,21 +612,15 @@ int fhmg_residual(fhmg_problem p, const double* u, const double* f, const double
   if (!u || !r) return fail(FHMG_EINVAL, "bad arrays");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
-  LevelData& lv = p->lev[p->nlev - 1];
-  fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M, u, F,
-                                                                                     nullptr, r);
-  ++p->launches;
-  CK(cudaGetLastError());
-  Geo geo{0, 0, 0, lv.npts, 0.0};
-  return launch_walk<double, fhmg::MODE_MATVEC>(p, p->h64.d, pick_tc(p->h64.d, lv.npts), geo, lv.npts,
-                                                const_cast<double*>(u), r, r, nullptr, nullptr);
+  double nrm;
+  return fine_defect(p, u, F, false, r, &nrm);
 }
 
 int fhmg_restrict_residual(fhmg_problem p, const double* u, const double* F, double* rc) {
   TRY(check_dims(p));
   if (p->nlev < 2) return fail(FHMG_EINVAL, "no coarser grid");
   if (!u || !F || !rc) return fail(FHMG_EINVAL, "bad arrays");
-  return restrict_defect(p, p->nlev - 1, u, F, rc);
+  return restrict_defect(p, p->nlev - 1, u, F, rc, false);
 }
 
 int fhmg_prolong_correct(fhmg_problem p, double* u, const double* e) {
@@ -569,7 +635,7 @@ int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int
   if (!u || nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0) return fail(FHMG_EINVAL, "bad arguments");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
-  return vcycle_rec(p, p->nlev - 1, u, F, nu1, nu2);
+  return vcycle_rec(p, p->nlev - 1, u, F, nu1, nu2, false);
 }
 
 int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const double* g, double* out) {
@@ -578,7 +644,7 @@ int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const d
   const double* F;
   TRY(full_rhs(p, f, g, &F));
   double v;
-  TRY(fine_norm(p, u, F, false, &v));
+  TRY(fine_defect(p, u, F, false, nullptr, &v));
   *out = v;
   return FHMG_OK;
 }
@@ -590,17 +656,12 @@ int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int 
     return fail(FHMG_EINVAL, "bad arguments");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
-  double r0, r;
-  TRY(fine_norm(p, u, F, false, &r0));
-  if (!std::isfinite(r0)) return fail(FHMG_ENAN, "initial residual is not finite");
-  r = r0;
   int k = 0;
-  while (r > rtol * r0 && k < max_cycles) {
-    TRY(vcycle_rec(p, p->nlev - 1, u, F, nu1, nu2));
-    TRY(fine_norm(p, u, F, nu2 > 0, &r));
-    ++k;
-    if (!std::isfinite(r)) return fail(FHMG_ENAN, "residual became non-finite after %d cycles", k);
-  }
+  double r0 = 0, r = 0;
+  if (p->prec == FHMG_MIXED_FP32)
+    TRY(solve_mixed(p, u, F, nu1, nu2, rtol, max_cycles, &k, &r0, &r));
+  else
+    TRY(solve_fp64(p, u, F, nu1, nu2, rtol, max_cycles, &k, &r0, &r));
   if (cycles_out) *cycles_out = k;
   if (relres_out) *relres_out = r0 > 0 ? r / r0 : 0.0;
   if (r > rtol * r0) return fail(FHMG_ENOTCONV, "relative residual %.3e after %d cycles", r0 > 0 ? r / r0 : 0.0, k);

@@ -6,6 +6,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <numeric>
 
 namespace fhmg {
@@ -468,6 +469,88 @@ void diag_inverses(const HostH& h, const FlatH& f, double shift, std::vector<dou
         X[(size_t)r * L + c] = -s / (D[(size_t)r * L + r] + shift);
       }
     }
+  }
+}
+
+}  // namespace fhmg
+
+namespace fhmg {
+namespace {
+
+void put_value(std::vector<unsigned char>& b, size_t off, double v, int elem_bytes) {
+  if (elem_bytes == 8) {
+    std::memcpy(&b[off], &v, 8);
+  } else {
+    float x = (float)v;
+    std::memcpy(&b[off], &x, 4);
+  }
+}
+
+size_t pad16(size_t n) { return (n + 15) & ~(size_t)15; }
+
+}  // namespace
+
+void build_panel(const HostH& h, const FlatH& f, int eb, PanelHost& out) {
+  const int L = f.L, nb = f.nb;
+  out = PanelHost();
+  out.cptr.assign(nb + 1, 0);
+  int maxdist = 0;
+  for (int i = 0; i < nb; ++i)
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) maxdist = std::max(maxdist, i - f.dlist_col[d]);
+  out.W = std::min(8, maxdist + 1);
+  auto add_chunk = [&](int type, int count, int aux, size_t bytes) -> size_t {
+    size_t off = out.pkg.size();
+    size_t nbytes = pad16(bytes);
+    out.pkg.resize(off + nbytes, 0);
+    out.chunks.push_back(type | (count << 4));
+    out.chunks.push_back(aux);
+    out.chunks.push_back((int)nbytes);
+    out.chunks.push_back((int)(off / 16));
+    out.slot_bytes = std::max(out.slot_bytes, (int)nbytes);
+    return off;
+  };
+  for (int i = 0; i < nb; ++i) {
+    // near-field blocks
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) {
+      const double* D = &f.dense_data[(size_t)f.dlist_blk[d] * L * L];
+      size_t off = add_chunk(CH_DENSE, L, f.dlist_col[d], (size_t)L * L * eb);
+      for (int k = 0; k < L; ++k)
+        for (int r = 0; r < L; ++r) put_value(out.pkg, off + ((size_t)k * L + r) * eb, D[(size_t)r * L + k], eb);
+    }
+    // U panel (row-major L x K in FlatH) in slabs of up to L columns
+    const int K = f.uptr[i + 1] - f.uptr[i];
+    for (int k0 = 0; k0 < K; k0 += L) {
+      const int kc = std::min(L, K - k0);
+      size_t off = add_chunk(CH_UPART, kc, k0, (size_t)kc * L * eb + (size_t)kc * 4);
+      for (int kk = 0; kk < kc; ++kk)
+        for (int r = 0; r < L; ++r)
+          put_value(out.pkg, off + ((size_t)kk * L + r) * eb, f.udata[f.uoff[i] + (size_t)r * K + k0 + kk], eb);
+      for (int kk = 0; kk < kc; ++kk) {
+        int z = f.uz[f.uptr[i] + k0 + kk];
+        std::memcpy(&out.pkg[off + (size_t)kc * L * eb + (size_t)kk * 4], &z, 4);
+      }
+    }
+    // diagonal block
+    {
+      const double* D = &f.dense_data[(size_t)f.diag_blk[i] * L * L];
+      size_t off = add_chunk(CH_DIAG, L, i, (size_t)L * L * eb);
+      for (int k = 0; k < L; ++k)
+        for (int r = 0; r < L; ++r) put_value(out.pkg, off + ((size_t)k * L + r) * eb, D[(size_t)r * L + k], eb);
+    }
+    // V panel (row-major K' x L in FlatH) in slabs of up to L rows
+    const int Kv = f.vptr[i + 1] - f.vptr[i];
+    for (int k0 = 0; k0 < Kv; k0 += L) {
+      const int kc = std::min(L, Kv - k0);
+      size_t off = add_chunk(CH_VPART, kc, k0, (size_t)kc * L * eb + (size_t)kc * 4);
+      for (int kk = 0; kk < kc; ++kk)
+        for (int c = 0; c < L; ++c)
+          put_value(out.pkg, off + ((size_t)kk * L + c) * eb, f.vdata[f.voff[i] + (size_t)(k0 + kk) * L + c], eb);
+      for (int kk = 0; kk < kc; ++kk) {
+        int code = 2 * f.vz[f.vptr[i] + k0 + kk] + f.vinit[f.vptr[i] + k0 + kk];
+        std::memcpy(&out.pkg[off + (size_t)kc * L * eb + (size_t)kk * 4], &code, 4);
+      }
+    }
+    out.cptr[i + 1] = (int)(out.chunks.size() / 4);
   }
 }
 

@@ -64,6 +64,28 @@ struct FlatH {
   long long flops_per_col_solve;
 };
 
+// The H-matrix as a stream of chunks that the panel kernel stages into shared memory, one
+// chunk per pipeline slot, in the order a leaf-row walk consumes them.  Per leaf row i:
+//   DENSE(j)  one L x L near-field block D_ij, column-major           (aux = j)
+//   UPART     up to L columns of the U panel, column-major, then their z-pool rows (int)
+//   DIAG      D_ii column-major (the smoother streams its level inverse instead) (aux = i)
+//   VPART     up to L rows of the V panel (row kk = V[kk][0..L)), then one int per row:
+//             2 * z-pool row + 1 if the row starts its block's z (assign, not add)
+// Chunk descriptor (4 ints): type | count << 4, aux, bytes, byte offset / 16.  Every chunk
+// starts on a 16-byte boundary and its size is a multiple of 16 bytes (TMA bulk copy rule).
+enum ChunkType { CH_DENSE = 0, CH_UPART = 1, CH_DIAG = 2, CH_VPART = 3 };
+
+struct PanelHost {
+  std::vector<unsigned char> pkg;
+  std::vector<int> chunks;   // 4 ints per chunk
+  std::vector<int> cptr;     // nb+1 chunk ranges per leaf row
+  int slot_bytes = 0;        // largest chunk
+  int W = 1;                 // depth of the ring of x tiles (max near-field distance + 1, <= 8)
+};
+
+// elem_bytes = 8 (FP64 matrices) or 4 (FP32 matrices)
+void build_panel(const HostH& h, const FlatH& f, int elem_bytes, PanelHost& out);
+
 // Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
 // Returns 0 on success, < 0 on invalid arguments.
 int build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,

@@ -92,15 +92,16 @@ __device__ __forceinline__ T reduce_splits(T v) {
 
 // Shared-memory layout, in bytes from the (16-byte aligned) dynamic base.
 struct PanelSmem {
-  size_t ys, ring, zp, bar, flag, total;
+  size_t ys, ysm, ring, zp, bar, flag, total;
 };
 __host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, int slot_bytes, int ns, int bT,
                                                 int bTM) {
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   PanelSmem s;
   s.ys = a16((size_t)ns * slot_bytes);
-  s.ring = a16(s.ys + (size_t)L * TC * bT);
-  s.zp = a16(s.ring + (size_t)W * L * TC * bT);
+  s.ysm = a16(s.ys + (size_t)L * TC * bT);
+  s.ring = a16(s.ysm + (size_t)L * TC * bTM);
+  s.zp = a16(s.ring + (size_t)W * L * TC * bTM);
   s.bar = a16(s.zp + (size_t)pool * TC * bTM);
   s.flag = s.bar + 8 * (size_t)ns;
   s.total = a16(s.flag + 16);
@@ -125,8 +126,9 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
   extern __shared__ __align__(16) unsigned char sm[];
   const PanelSmem lay = panel_smem(L, TC, P.pool, P.W, P.slot_bytes, P.ns, sizeof(T), sizeof(TM));
   unsigned char* slots = sm;
-  T* ys = reinterpret_cast<T*>(sm + lay.ys);
-  T* ring = reinterpret_cast<T*>(sm + lay.ring);
+  T* ys = reinterpret_cast<T*>(sm + lay.ys);     // y / x of the current leaf (T)
+  TM* ysm = reinterpret_cast<TM*>(sm + lay.ysm);  // the same in TM, converted once per leaf
+  TM* ring = reinterpret_cast<TM*>(sm + lay.ring);
   TM* zp = reinterpret_cast<TM*>(sm + lay.zp);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + lay.bar);
   volatile int* sflag = reinterpret_cast<volatile int*>(sm + lay.flag);
@@ -238,11 +240,11 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
           const TM* D = reinterpret_cast<const TM*>(buf);
           const int j = cd.y;
           if (i - j < P.W) {
-            const T* xr = ring + (size_t)(j % P.W) * L * TC;
+            const TM* xr = ring + (size_t)(j % P.W) * L * TC;
 #pragma unroll
             for (int kk = 0; kk < KS; ++kk) {
               const int k = sp + kk * S;
-              const TM xv = (TM)xr[k * TC + cl];
+              const TM xv = xr[k * TC + cl];
 #pragma unroll
               for (int q = 0; q < Q; ++q) part[q][kk % NA] += D[k * L + rg + RG * q] * xv;
             }
@@ -275,11 +277,14 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
             for (int a = 1; a < NA; ++a) s += part[q][a];
             acc[q] = reduce_splits<T, TC, S>(acc[q] - (T)s);
           }
-          T* xr_i = ring + (size_t)(i % P.W) * L * TC;
+          TM* xr_i = ring + (size_t)(i % P.W) * L * TC;
           if (MODE == MODE_SMOOTH) {
             if (sp == 0) {
 #pragma unroll
-              for (int q = 0; q < Q; ++q) ys[(rg + RG * q) * TC + cl] = acc[q];
+              for (int q = 0; q < Q; ++q) {
+                ys[(rg + RG * q) * TC + cl] = acc[q];
+                ysm[(rg + RG * q) * TC + cl] = (TM)acc[q];
+              }
             }
             __syncthreads();
 #pragma unroll
@@ -291,7 +296,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
 #pragma unroll
               for (int kk = 0; kk < KS; ++kk) {
                 const int k = sp + kk * S;
-                if (ddiag ? k < r : k <= r) s[kk % NA] += Dd[k * L + r] * (TM)ys[k * TC + cl];
+                if (ddiag ? k < r : k <= r) s[kk % NA] += Dd[k * L + r] * ysm[k * TC + cl];
               }
               TM s1 = s[0];
 #pragma unroll
@@ -305,8 +310,9 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
 #pragma unroll
               for (int q = 0; q < Q; ++q) {
                 const int r = rg + RG * q;
-                ys[r * TC + cl] = acc[q];
-                xr_i[r * TC + cl] = acc[q];
+                const TM xm = (TM)acc[q];
+                ysm[r * TC + cl] = xm;
+                xr_i[r * TC + cl] = xm;
                 if (valid) X[(long long)(i * L + r) * ld + p] = acc[q];
               }
             }
@@ -315,8 +321,10 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
 #pragma unroll
               for (int q = 0; q < Q; ++q) {
                 const int r = rg + RG * q;
+                const TM xm = (TM)xcur[q];
                 ys[r * TC + cl] = xcur[q];
-                xr_i[r * TC + cl] = xcur[q];
+                ysm[r * TC + cl] = xm;
+                xr_i[r * TC + cl] = xm;
               }
             }
             __syncthreads();
@@ -329,7 +337,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
 #pragma unroll
               for (int kk = 0; kk < KS; ++kk) {
                 const int k = sp + kk * S;
-                if (ddiag ? k < r : k <= r) s[kk % NA] += Dd[k * L + r] * (TM)ys[k * TC + cl];
+                if (ddiag ? k < r : k <= r) s[kk % NA] += Dd[k * L + r] * ysm[k * TC + cl];
               }
               TM s1 = s[0];
 #pragma unroll
@@ -356,7 +364,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
             TM s = 0;
             if (o < O) {
               const int kk = o / TC, cc = o % TC;
-              for (int k = sv; k < L; k += Sv) s += V[kk * L + k] * (TM)ys[k * TC + cc];
+              for (int k = sv; k < L; k += Sv) s += V[kk * L + k] * ysm[k * TC + cc];
             }
             for (int w = Sv >> 1; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
             if (o < O && sv == 0) {

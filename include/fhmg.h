@@ -122,6 +122,15 @@ int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int
 /* ||f + d g - A_{h,tau} u||_inf into *out_max (host). */
 int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const double* g,
                        double* out_max);
+/* The same max-norm for callers that cannot allocate device memory once their loop runs (a fixed
+ * budget reserved up front, a real-time loop, a host framework that owns every allocation).  The
+ * paper has no counterpart: this is a library service.  It allocates nothing: its scratch is a
+ * fixed library-owned device array of 2^21 doubles (16 MiB, held on every GPU that loads the
+ * library until the process exits), so M * N^dim must be <= 2^21 (else FHMG_EINVAL).  f is the
+ * full right-hand side (fold any initial data into it: there is no g).  The first call on a device
+ * looks the array's address up -- make it before any stream capture.  All calls share the array:
+ * calls whose GPU work overlaps race and must be serialised by the caller. */
+int fhmg_residual_norm_noalloc(fhmg_problem p, const double* u, const double* f, double* out_max);
 /* V(nu1, nu2) cycles from the initial guess in u until ||r_k||_inf <= rtol ||r_0||_inf or
  * max_cycles.  cycles_out / relres_out (host, may be NULL) receive the cycle count and
  * ||r_k||/||r_0||.  With prec FHMG_MIXED_FP32 the cycles run in FP32 on the correction

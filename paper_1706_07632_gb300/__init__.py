@@ -50,6 +50,7 @@ _SIGS = {
     "fhmg_prolong_correct": (_I, [_P, _P, _P]),
     "fhmg_vcycle": (_I, [_P, _P, _P, _P, _I, _I]),
     "fhmg_residual_norm": (_I, [_P, _P, _P, _P, _c.POINTER(_D)]),
+    "fhmg_residual_norm_noalloc": (_I, [_P, _P, _P, _c.POINTER(_D)]),
     "fhmg_solve": (_I, [_P, _P, _P, _P, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
     "fhmg_solve_host": (_I, [_P, _P, _P, _P, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
 }
@@ -196,6 +197,12 @@ class Problem:
     def residual_norm(self, u, f, g=None):
         v = _D()
         _check(lib().fhmg_residual_norm(self._p, _ptr(u), _ptr(f), _ptr(g), ctypes.byref(v)))
+        return v.value
+
+    def residual_norm_noalloc(self, u, f):
+        """fhmg_residual_norm_noalloc: same norm, scratch from a fixed library-owned device array."""
+        v = _D()
+        _check(lib().fhmg_residual_norm_noalloc(self._p, _ptr(u), _ptr(f), ctypes.byref(v)))
         return v.value
 
     def solve(self, u, f, g=None, nu1=1, nu2=1, rtol=1e-10, max_cycles=50, allow_notconv=False):

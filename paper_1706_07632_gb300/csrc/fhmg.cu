@@ -383,6 +383,32 @@ __global__ void scale_kernel(double* y, long long n, double a) {
 
 }  // namespace
 
+// Internal hook for entry points that supply their own scratch (noalloc.cu): the FP64 defect of
+// u against F at every finest-grid point written to B (device, M * N^dim doubles), its max-norm
+// folded into *norm_word (zeroed here) and returned in *out.  Launches kernels and copies 8 bytes
+// to the host; allocates nothing.
+int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, double* B,
+                              unsigned long long* norm_word, double* out) {
+  LevelData& lv = p->lev[p->nlev - 1];
+  CK(cudaMemsetAsync(norm_word, 0, sizeof(unsigned long long), p->st));
+  fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
+                                                                                     u, F, nullptr, B);
+  ++p->launches;
+  CK(cudaGetLastError());
+  TRY(walk_matvec(p, false, lv.npts, u, B, nullptr, norm_word));
+  unsigned long long bits = 0;
+  int derr = 0;
+  CK(cudaMemcpyAsync(&bits, norm_word, sizeof bits, cudaMemcpyDeviceToHost, p->st));
+  CK(cudaMemcpyAsync(&derr, p->derr, sizeof derr, cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  if (derr) return fail(FHMG_ETIMEOUT, "a panel kernel gave up waiting on a shared-memory stage");
+  std::memcpy(out, &bits, sizeof bits);
+  return FHMG_OK;
+}
+
+long long fhmg_internal_grid_elems(fhmg_problem p) { return p->lev[p->nlev - 1].npts * (long long)p->M; }
+int fhmg_internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 // ================================================================ C-ABI
 
 extern "C" {

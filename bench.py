@@ -1,25 +1,26 @@
-"""Benchmark: space-time DOF * cycles / s of the multigrid waveform-relaxation solve.
+"""Benchmark: space-time DOF * cycles / s (time-to-1e-8 solve) of multigrid waveform relaxation.
 
-Workload (default): 1D time-fractional heat equation, N = 4095 interior points, M = 4096 graded
-time steps, alpha = 0.5, gamma = (2 - alpha)/alpha, H-matrix with leaf 64 and recompression
-tolerance 1e-10, manufactured u = t^alpha sin(pi x), zero initial guess, V(1,1) cycles until the
-max-norm residual drops by 1e-8.  One step = one complete solve (all hot-path kernels: smoother
-half-sweeps, residual + restriction, prolongation, coarsest solve, residual norms).
+Headline workload: 1D time-fractional heat equation, N = 4095 interior points, M = 4096 graded time
+steps, alpha = 0.5, gamma = (2 - alpha)/alpha = 3, H-matrix leaf 64 with recompression tolerance
+1e-10, manufactured u = t^alpha sin(pi x), zero initial guess, V(1,1) cycles until the max-norm
+residual drops by 1e-8.  One step = one complete solve: every hot-path kernel (smoother
+half-sweeps, defect + restriction, prolongation, coarsest solve, defect norms) runs inside it.
+Also measured (key "workload_2d"): the 2D workload N = 511^2, M = 1024, alpha = 0.4, gamma = 2.5.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--alpha A]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-2d]
 
-value       = DOF * cycles summed over the K timed solves / device time (CUDA events, max over
-              ranks), DOF = N * M.  Inputs (u, f: 134 MB each) exceed the 129 MB L2.
-e2e         = the same metric through fhmg_solve_host with pinned host buffers (the H2D copy of u
-              and f and the D2H copy of u inside the timed region).
-roofline    = the finest-grid smoother kernel (the dominant launch), FP64-ALU bound: algorithmic
-              FP64 flops per launch / its CUDA-event time, against 152 SMs x 2 DFMA/clk x 2 flop
-              x 2.07 GHz = 1.258 TFLOP/s.
-cpu_baseline / --impl reference = the CPU oracle's direct solve (implicit time stepping with the
-              dense L1 history sum) on the host cores, expressed as DOF * (the GPU's cycle count)
-              / s so that the ratio is a time-to-solution ratio.
-N > 1 (torchrun): replicas only -- every rank solves its own instance, no collective on the data
-path; value is the sum over ranks.
+value     = DOF * K_ref * ranks / (device time per solve), K_ref = the FP64 V(1,1) cycle count of
+            the workload (8 for the headline), so every arm and path is compared on
+            time-to-solution in one unit.  value is the mixed-precision path (defect correction,
+            FP32 H-matrix products, FP64 defect); the FP64 path is reported beside it.
+e2e       = the same metric through fhmg_solve_host (pinned host buffers; H2D of u and f and D2H
+            of u inside the timed region).
+roofline  = the finest-grid smoother launches (the dominant kernel), timed live with CUDA events
+            on the launching stream inside the timed solves.
+cpu_baseline / --impl reference = the oracle's direct solve (implicit time stepping with the dense
+            L1 history sum, numpy/OpenBLAS) of the same workload on the host cores.
+N > 1 (torchrun): replicas only -- each rank solves its own instance; no data-path collective.
+Inputs (u, f: 134 MB each in 1D, 2.1 GB in 2D) exceed the 129 MB L2.
 """
 from __future__ import annotations
 
@@ -36,9 +37,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # 1.258, DFMA units x clock
-MEASURED_DFMA_TFLOPS = 1.202                        # dependent-free DFMA loop on this machine's GB300
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5, FFMA units x clock (a loop measured 75.1)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # 1.258: DFMA units x clock (a DFMA loop measured 1.202)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: FFMA units x clock (an FFMA loop measured 75.1)
+REF_CYCLES_1D = 8   # FP64 V(1,1) cycles to 1e-8 on the headline workload, measured on GB300
 
 
 def parse():
@@ -53,13 +54,14 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-2d", action="store_true")
     return ap.parse_args()
 
 
 def workload(a):
     gamma = (2 - a.alpha) / a.alpha
-    return {"workload": f"1D H-matrix FP64, N={a.N}, M={a.M}, alpha={a.alpha}, gamma={gamma:.4g}, "
-                        f"leaf 64, tol 1e-10, V(1,1) to relres {a.rtol:g}",
+    return {"workload": f"1D H-matrix, N={a.N}, M={a.M}, alpha={a.alpha}, gamma={gamma:.4g}, leaf 64, tol 1e-10, "
+                        f"V(1,1) to relres {a.rtol:g}",
             "dim": 1, "N": a.N, "M": a.M, "alpha": a.alpha, "gamma": gamma, "leaf": 64, "tol": 1e-10,
             "cycle": "V(1,1)", "rtol": a.rtol, "source": "manufactured t^alpha sin(pi x)",
             "l2": "inputs larger than L2 (u, f 134 MB each)"}
@@ -106,7 +108,7 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(a):
+def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
@@ -118,8 +120,8 @@ def dist_setup(a):
     return None, 0, 1
 
 
-def oracle_direct_sample(a, cores_env=None):
-    """Times the oracle's direct solve of the full workload (dense R history, O1)."""
+def oracle_direct_sample(a):
+    """Times the oracle's direct solve of the full headline workload (dense R history, O1)."""
     import numpy as np
     from oracle import direct, l1
     from paper_1706_07632_gb300 import inputs
@@ -137,52 +139,47 @@ def oracle_direct_sample(a, cores_env=None):
 
 
 def run_reference(a):
-    """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
-    dist, rank, ws = dist_setup(a)
+    """--impl reference: the CPU oracle on the host cores (rank 0 only; other ranks exit)."""
+    dist, rank, ws = dist_setup()
     if rank != 0:
         return
-    # the cycle unit of the metric: FP64 V(1,1) cycles to 1e-8 measured on GB300 for the default
-    # workload (other workloads: set FHMG_REF_CYCLES)
-    cyc = int(os.environ.get("FHMG_REF_CYCLES", "8"))
+    cyc = int(os.environ.get("FHMG_REF_CYCLES", str(REF_CYCLES_1D)))
     dof = a.N * a.M
     for _ in range(max(0, min(a.warmup, 1))):
         oracle_direct_sample(a)
-    times = []
-    for _ in range(a.steps):
-        ts, tb = oracle_direct_sample(a)
-        times.append(ts)
+    times = [oracle_direct_sample(a)[0] for _ in range(a.steps)]
     tot = sum(times)
     value = dof * cyc * a.steps / tot
-    cores = os.cpu_count()
+    sample = (f"full direct solve N={a.N} M={a.M} per step (implicit time stepping, dense L1 history, numpy/OpenBLAS "
+              f"on all host threads); DOF*cycles with the FP64 cycle count {cyc}")
     line = {"impl": "reference", "metric": "space-time DOF*cycles/s (time-to-1e-8 solve)", "value": value,
             "unit": "DOF*cycles/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": workload(a),
-            "cpu_baseline": {"value": value, "unit": "DOF*cycles/s", "cores": cores, "kind": "oracle",
-                             "sample": f"full direct solve N={a.N} M={a.M} (implicit time stepping, dense L1 history, "
-                                       f"numpy/OpenBLAS); DOF*cycles with {cyc} cycles = the GPU FP64 count"},
+            "cpu_baseline": {"value": value, "unit": "DOF*cycles/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "DOF*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def timed_solves(P, f, a, stream, rank, dist):
-    """W untimed + K timed solves from u = 0 on one problem; CUDA events on the launching stream."""
+def timed_solves(P, f, steps, warmup, rtol, stream, dist):
+    """warmup untimed + steps timed solves from u = 0; CUDA events on the launching stream."""
     import torch
     u = torch.zeros_like(f)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         u.zero_()
-        P.solve(u, f, None, 1, 1, a.rtol, 80)
+        P.solve(u, f, None, 1, 1, rtol, 80)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     P.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cycles, rr_last = 0, None
+    cycles, rr = 0, None
     e0.record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         u.zero_()
-        k, rr_last = P.solve(u, f, None, 1, 1, a.rtol, 80)
+        k, rr = P.solve(u, f, None, 1, 1, rtol, 80)
         cycles += k
     e1.record(stream)
     torch.cuda.synchronize()
@@ -190,7 +187,48 @@ def timed_solves(P, f, a, stream, rank, dist):
     P.profile(False)
     if dist:
         dist.barrier()
-    return e0.elapsed_time(e1), cycles, rr_last, cnt, u
+    ms = e0.elapsed_time(e1)
+    if dist:
+        mx = torch.tensor([ms], device=f.device)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        ms = float(mx[0])
+    return {"ms": ms, "cycles": cycles, "relres": rr, "cnt": cnt, "u": u}
+
+
+def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, dist, dev):
+    import torch
+    t0 = time.perf_counter()
+    H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
+    t_hbuild = time.perf_counter() - t0
+    tmesh, _ = H.mesh()
+    amp, s = inputs.manufactured(tmesh[1:], N, dim, alpha)
+    f = torch.as_tensor(amp, device=dev).reshape((-1,) + (1,) * dim) * torch.as_tensor(s, device=dev)[None]
+    res = {}
+    for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
+        P = fh.Problem(H, dim, N, 1.0, prec, stream)
+        r = timed_solves(P, f, steps, warmup, rtol, stream, dist)
+        r["P"] = P
+        r["time_to_rtol_s"] = r["ms"] / steps / 1e3
+        res[name] = r
+        del r["u"]
+    return H, f, res, t_hbuild
+
+
+def roofline(H, r, ncols_avg, kind):
+    c = r["cnt"]
+    flops_launch = H.flops_per_column() * ncols_avg
+    sm_ms = c["smooth_ms"] / max(c["smooth_launches"], 1)
+    achieved = flops_launch / (sm_ms / 1e3) / 1e12
+    if kind == "fp64":
+        peak, note = FP64_PEAK_TFLOPS, "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured 1.202)"
+        kern = "hpanel_kernel<double,double,64,*,SMOOTH> (finest-grid half-sweep)"
+    else:
+        peak, note = FP32_PEAK_TFLOPS, "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (an FFMA loop measured 75.1)"
+        kern = "hpanel_kernel<*,float,64,*,SMOOTH> (finest-grid half-sweep, FP32 products)"
+    return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_note": note, "traffic": None, "avg_launch_ms": sm_ms,
+            "launches_timed": c["smooth_launches"], "algorithmic_flops_per_launch": flops_launch,
+            "share_of_step": c["smooth_ms"] / r["ms"] if r["ms"] > 0 else None}
 
 
 def main():
@@ -204,56 +242,21 @@ def main():
     import paper_1706_07632_gb300 as fh
     from paper_1706_07632_gb300 import inputs
 
-    dist, rank, ws = dist_setup(a)
+    dist, rank, ws = dist_setup()
     dev = torch.device("cuda", torch.cuda.current_device())
-    gamma = (2 - a.alpha) / a.alpha
-    t_h0 = time.perf_counter()
-    H = fh.HMatrix(a.alpha, gamma, 1.0, a.M, 64, 0, 1e-10)
-    t_hbuild = time.perf_counter() - t_h0
     stream = torch.cuda.current_stream()
-    tmesh, _ = H.mesh()
-    amp, s = inputs.manufactured(tmesh[1:], a.N, 1, a.alpha)
-    f = torch.as_tensor(amp, device=dev)[:, None] * torch.as_tensor(s, device=dev)[None, :]
+    gamma = (2 - a.alpha) / a.alpha
     dof = a.N * a.M
 
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    res = {}
-    for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
-        P = fh.Problem(H, 1, a.N, 1.0, prec, stream)
-        ms, cycles, rr, cnt, u = timed_solves(P, f, a, stream, rank, dist)
-        if dist:
-            mx = torch.tensor([ms], device=dev)
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            ms = float(mx[0])
-        res[name] = {"P": P, "ms": ms, "cycles": cycles, "relres": rr, "cnt": cnt}
+    H, f, res, t_hbuild = measure(fh, inputs, 1, a.N, a.M, a.alpha, gamma, a.steps, a.warmup, a.rtol, stream, dist, dev)
     clk = clocks.stop() if clocks else None
 
-    # common cycle unit: the FP64 V(1,1) cycle count of this workload
     k_ref = res["fp64"]["cycles"] / a.steps
-    for name in res:
-        r = res[name]
-        r["time_to_rtol_s"] = r["ms"] / a.steps / 1e3
+    for r in res.values():
         r["value"] = dof * k_ref * ws / r["time_to_rtol_s"]
     head = res["mixed"]
-    value = head["value"]
 
-    def roofline(r, kind):
-        c = r["cnt"]
-        flops_launch = H.flops_per_column() * (a.N / 2.0)
-        sm_ms = c["smooth_ms"] / max(c["smooth_launches"], 1)
-        achieved = flops_launch / (sm_ms / 1e3) / 1e12
-        if kind == "fp64":
-            peak, note = FP64_PEAK_TFLOPS, "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured 1.202)"
-            kern = "hwalk_kernel<double,double,64,*,SMOOTH> (finest-grid half-sweep)"
-        else:
-            peak, note = FP32_PEAK_TFLOPS, "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (an FFMA loop measured 75.1)"
-            kern = "hwalk_kernel<double,float,64,*,SMOOTH> (finest-grid half-sweep, FP32 products)"
-        return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_note": note, "traffic": None, "avg_launch_ms": sm_ms,
-                "launches_timed": c["smooth_launches"], "algorithmic_flops_per_launch": flops_launch,
-                "share_of_step": c["smooth_ms"] / r["ms"] if r["ms"] > 0 else None}
-
-    # end to end through the C-ABI with host buffers (headline path)
     e2e = None
     if not a.no_e2e:
         P = head["P"]
@@ -268,30 +271,52 @@ def main():
         te = time.perf_counter() - t0
         e2e = {"value": dof * k_ref * ws * a.steps / te, "unit": "DOF*cycles/s", "h2d_bytes_per_step": 2 * dof * 8,
                "d2h_bytes_per_step": dof * 8, "ms_per_step": 1e3 * te / a.steps}
+        del fh_host, uh
+
+    def summary(r, steps):
+        return {"value": r.get("value"), "time_to_rtol_s": r["time_to_rtol_s"],
+                "cycles_per_solve": r["cycles"] / steps, "relres": r["relres"],
+                "gpu_launches_per_solve": r["cnt"]["launches"] / steps}
+
+    w2d = None
+    if not a.no_2d:
+        del f
+        torch.cuda.empty_cache()
+        N2, M2, al2, ga2 = 511, 1024, 0.4, 2.5
+        st2, wu2 = min(a.steps, 2), 1
+        H2, f2, res2, tb2 = measure(fh, inputs, 2, N2, M2, al2, ga2, st2, wu2, a.rtol, stream, dist, dev)
+        k2 = res2["fp64"]["cycles"] / st2
+        dof2 = N2 * N2 * M2
+        for r in res2.values():
+            r["value"] = dof2 * k2 * ws / r["time_to_rtol_s"]
+        w2d = {"workload": f"2D H-matrix, N={N2}^2, M={M2}, alpha={al2}, gamma={ga2}, leaf 64, tol 1e-10, V(1,1) to "
+                           f"relres {a.rtol:g}",
+               "fp64": summary(res2["fp64"], st2), "mixed": summary(res2["mixed"], st2),
+               "speedup_mixed_vs_fp64": res2["fp64"]["time_to_rtol_s"] / res2["mixed"]["time_to_rtol_s"],
+               "roofline_fp64": roofline(H2, res2["fp64"], N2 * N2 / 2.0, "fp64"),
+               "roofline_mixed": roofline(H2, res2["mixed"], N2 * N2 / 2.0, "mixed"), "hbuild_s": tb2}
+        del f2
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         ts, tb = oracle_direct_sample(a)
         cpu = {"value": dof * k_ref / ts, "unit": "DOF*cycles/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"full direct solve of this workload (N={a.N}, M={a.M}), implicit time stepping with the "
-                         f"dense L1 history sum, numpy/OpenBLAS on all host threads: {ts:.2f} s (+{tb:.2f} s to "
+               "sample": f"full direct solve of the headline workload (N={a.N}, M={a.M}), implicit time stepping with "
+                         f"the dense L1 history sum, numpy/OpenBLAS on all host threads: {ts:.2f} s (+{tb:.2f} s to "
                          f"build R, not timed); cycles = the FP64 V(1,1) count to 1e-8 ({k_ref:.0f})"}
 
     if rank == 0:
-        def summary(r):
-            return {"value": r["value"], "time_to_rtol_s": r["time_to_rtol_s"], "cycles_per_solve": r["cycles"] / a.steps,
-                    "relres": r["relres"], "gpu_launches_per_solve": r["cnt"]["launches"] / a.steps}
-        line = {"metric": "space-time DOF*cycles/s (time-to-1e-8 solve)", "value": value, "unit": "DOF*cycles/s",
-                "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": head["ms"] / a.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
-                "data": "synthetic", "config": workload(a),
-                "headline": "mixed: FP64 defect correction, FP32 H-matrix products in the V-cycles",
+        line = {"metric": "space-time DOF*cycles/s (time-to-1e-8 solve)", "value": head["value"],
+                "unit": "DOF*cycles/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": head["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": workload(a),
+                "headline": "mixed precision: FP64 defect correction around V-cycles with FP32 H-matrix products",
                 "cycle_unit": f"FP64 V(1,1) cycles to relres {a.rtol:g} on this workload = {k_ref:.0f}",
-                "fp64": summary(res["fp64"]), "mixed": summary(res["mixed"]),
+                "fp64": summary(res["fp64"], a.steps), "mixed": summary(res["mixed"], a.steps),
                 "speedup_mixed_vs_fp64": res["fp64"]["time_to_rtol_s"] / res["mixed"]["time_to_rtol_s"],
-                "hbuild_s": t_hbuild, "roofline": roofline(res["mixed"], "mixed"),
-                "roofline_fp64": roofline(res["fp64"], "fp64"), "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": head["cnt"]["launches"], "clocks": clk}
+                "hbuild_s": t_hbuild, "roofline": roofline(H, res["mixed"], a.N / 2.0, "mixed"),
+                "roofline_fp64": roofline(H, res["fp64"], a.N / 2.0, "fp64"), "workload_2d": w2d,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": head["cnt"]["launches"], "clocks": clk}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

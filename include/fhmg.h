@@ -88,8 +88,12 @@ int fhmg_problem_destroy(fhmg_problem p);
 /* Chooses the column tile of each kernel by timing (autotuner); optional. */
 int fhmg_problem_autotune(fhmg_problem p);
 /* Mixed path: V-cycles run on the correction equation between two FP64 defect evaluations
- * (default 3, >= 1). */
+ * (>= 1; 0 restores the default: 2 with FP32 storage, 4 with FP64 storage). */
 int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles);
+/* Mixed path, storage of the inner cycles: 0 automatic (FP32 when 6e-8 * 4 (N+1)^2 / pi^2 <= 0.05,
+ * i.e. N <= 1023), 1 FP64 grid functions / stencil / diagonal with FP32 H-matrix products,
+ * 2 FP32 throughout.  The outer defect and the update of u are FP64 in every mode. */
+int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode);
 /* Resets the counters below and, if enable != 0, records CUDA events on the problem's stream
  * around every smoother launch on the finest grid (the dominant kernel). */
 int fhmg_problem_profile(fhmg_problem p, int enable);
@@ -138,6 +142,20 @@ int fhmg_residual_norm_noalloc(fhmg_problem p, const double* u, const double* f,
  * *cycles_out then counts inner cycles. */
 int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int nu1, int nu2,
                double rtol, int max_cycles, int* cycles_out, double* relres_out);
+/* Solves n independent problems together (1 <= n <= 4096; each with its own H-matrix, alpha,
+ * gamma, M, N; all FHMG_FP64 or all FHMG_MIXED_FP32).  Their V-cycles advance in lockstep by
+ * depth below each finest grid: every smoother colour, every coarse-grid product and every
+ * defect of all instances is ONE persistent panel-kernel launch (one per leaf size present);
+ * one cycle of all active instances is captured into a CUDA graph and replayed.  Mixed: defect
+ * correction with FP32 H-matrix products (FP64 grid functions) and FP64 defects.  u[i], f[i]
+ * device arrays of problem i; cycles_out / relres_out (n host entries each, may be NULL).
+ * Runs on an internal stream ordered after, and before, every problem's stream. */
+int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f, int nu1, int nu2,
+                       double rtol, int max_cycles, int* cycles_out, double* relres_out);
+/* Autotuner for the leaf size: builds the H-matrix with leaf 32 and 64, autotunes the column
+ * tiles of each, times one V-cycle, and returns the faster leaf (and its cycle time in ms). */
+int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, int dim, int N, double Lx,
+                       int prec, void* stream, int* best_leaf, double* best_ms);
 /* fhmg_solve with HOST arrays (u in/out, f, g or NULL): copies in, solves, copies u back. */
 int fhmg_solve_host(fhmg_problem p, double* u_host, const double* f_host, const double* g_host,
                     int nu1, int nu2, double rtol, int max_cycles, int* cycles_out,

@@ -41,6 +41,7 @@ _SIGS = {
     "fhmg_problem_autotune": (_I, [_P]),
     "fhmg_problem_profile": (_I, [_P, _I]),
     "fhmg_problem_set_inner": (_I, [_P, _I]),
+    "fhmg_problem_set_mixed_storage": (_I, [_P, _I]),
     "fhmg_problem_counters": (_I, [_P, _c.POINTER(_LL), _c.POINTER(_LL), _c.POINTER(_D)]),
     "fhmg_line_solve": (_I, [_P, _I, _P, _P, _LL]),
     "fhmg_hmatvec": (_I, [_P, _P, _P, _LL]),
@@ -53,6 +54,9 @@ _SIGS = {
     "fhmg_residual_norm_noalloc": (_I, [_P, _P, _P, _c.POINTER(_D)]),
     "fhmg_solve": (_I, [_P, _P, _P, _P, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
     "fhmg_solve_host": (_I, [_P, _P, _P, _P, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
+    "fhmg_solve_batched": (_I, [_I, _c.POINTER(_P), _c.POINTER(_P), _c.POINTER(_P), _I, _I, _D, _I,
+                                _c.POINTER(_I), _c.POINTER(_D)]),
+    "fhmg_autotune_leaf": (_I, [_D, _D, _D, _I, _D, _I, _I, _D, _I, _P, _c.POINTER(_I), _c.POINTER(_D)]),
 }
 
 
@@ -164,6 +168,10 @@ class Problem:
     def set_inner(self, cycles):
         _check(lib().fhmg_problem_set_inner(self._p, cycles))
 
+    def set_mixed_storage(self, mode):
+        """0 automatic, 1 FP64 storage with FP32 products, 2 FP32 throughout (inner cycles)."""
+        _check(lib().fhmg_problem_set_mixed_storage(self._p, mode))
+
     def profile(self, enable=True):
         _check(lib().fhmg_problem_profile(self._p, 1 if enable else 0))
 
@@ -223,3 +231,25 @@ class Problem:
         if getattr(self, "_p", None) and _lib is not None:
             _lib.fhmg_problem_destroy(self._p)
             self._p = None
+
+
+def solve_batched(problems, us, fs, nu1=1, nu2=1, rtol=1e-8, max_cycles=60, allow_notconv=False):
+    """fhmg_solve_batched: all problems' V-cycles in lockstep, one launch per stage, graph-replayed.
+    Returns (cycles, relres) lists."""
+    n = len(problems)
+    P = (_P * n)(*[p._p for p in problems])
+    U = (_P * n)(*[_ptr(u) for u in us])
+    F = (_P * n)(*[_ptr(f) for f in fs])
+    k = (_I * n)()
+    rr = (_D * n)()
+    st = lib().fhmg_solve_batched(n, P, U, F, nu1, nu2, rtol, max_cycles, k, rr)
+    _check(st, allow=(FHMG_ENOTCONV,) if allow_notconv else ())
+    return list(k), list(rr)
+
+
+def autotune_leaf(alpha, gamma, T, M, tol, dim, N, Lx=1.0, prec=FP64, stream=None):
+    """fhmg_autotune_leaf: (best leaf size, its V-cycle time in ms)."""
+    leaf, ms = _I(), _D()
+    _check(lib().fhmg_autotune_leaf(alpha, gamma, T, M, tol, dim, N, Lx, prec, _stream_ptr(stream),
+                                    ctypes.byref(leaf), ctypes.byref(ms)))
+    return leaf.value, ms.value

@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fhmg.h"
@@ -64,6 +66,8 @@ struct LevelData {
   double h = 0, inv_h2 = 0, shift = 0;
   double* E = nullptr;         // unknown of the coarse-grid correction (coarse levels)
   double* RC = nullptr;        // restricted defect (coarse levels)
+  float* E32 = nullptr;        // FP32 copies for the FP32 inner cycles of the mixed path
+  float* RC32 = nullptr;
   double* Dinv64 = nullptr;    // (D_ii + s I)^{-1}, FP64, column-major
   float* Dinv32 = nullptr;     // the same in FP32 (mixed path; its diagonal is not used)
   double* dinvdiag = nullptr;  // FP64 diagonal of the inverses (mixed path)
@@ -84,6 +88,11 @@ struct fhmg_problem_s {
   double* Xs = nullptr;  // scratch, >= max(colour-0 count, coarse count) * M
   double* Rs = nullptr;  // scratch, fine points * M (defect)
   double* Ef = nullptr;  // fine-grid correction of the mixed path
+  float* Xs32 = nullptr; // FP32 inner cycles of the mixed path: scratch, defect, correction
+  float* Rs32 = nullptr;
+  float* Ef32 = nullptr;
+  int mixed_storage = 0; // 0 automatic, 1 FP64 storage + FP32 products, 2 FP32 storage
+  std::map<std::pair<int, long long>, int> tune;  // autotuned column tiles: (kind*2+mode, ncols) -> TC
   double* Ff = nullptr;  // f + d g when g is given
   double* dmm = nullptr; // d_{m,m}
   unsigned long long* dnorm = nullptr;
@@ -91,7 +100,7 @@ struct fhmg_problem_s {
   double* hu = nullptr;  // device copies for fhmg_solve_host
   double* hf = nullptr;
   double* hg = nullptr;
-  int inner = 3;         // inner V-cycles per defect-correction step (mixed path)
+  int inner = 0;         // inner V-cycles per defect-correction step (0: 2 with FP32 storage, 4 otherwise)
   std::vector<void*> allocs;
   long long launches = 0;       // kernel launches issued (all kernels)
   bool profile = false;         // record events around finest-level smoother walks
@@ -174,55 +183,116 @@ int walk_status(int s, const std::string& err) {
   return fail(s == 1 ? FHMG_ECUDA : FHMG_EINVAL, "%s", err.c_str());
 }
 
-int walk(fhmg_problem p, bool mixed, fhmg::WalkArgs& a) {
-  if (a.ncols <= 0) return FHMG_OK;
-  std::string err;
-  ++p->launches;
-  a.err = p->derr;
-  a.tile = 0;
-  if (mixed) {
-    a.P = p->panel32.d;
-    return walk_status(fhmg::walk_launch_df(p->st, a, &err, nullptr), err);
-  }
-  a.P = p->panel64.d;
-  return walk_status(fhmg::walk_launch_dd(p->st, a, &err, nullptr), err);
+// Arithmetic of a walk: K64 FP64 storage and products; KSPLIT FP64 storage, FP32 products;
+// K32 FP32 storage and products (inner cycles on well-conditioned grids).
+enum { K64 = 0, KSPLIT = 1, K32 = 2 };
+
+// Column tile chosen by the autotuner for (kind, mode, ncols), 0 if none (automatic).
+int tuned_tile(fhmg_problem p, int kind, int mode, long long nc) {
+  auto it = p->tune.find(std::make_pair(kind * 2 + mode, nc));
+  return it == p->tune.end() ? 0 : it->second;
 }
 
-// One smoother half-sweep / line solve walk on level l (shift of that level).
-int walk_smooth(fhmg_problem p, int l, bool mixed, const Geo& g, long long nc, double* X, const double* B) {
+// per-type level buffers
+template <typename T> T* lev_E(LevelData& lv);
+template <> double* lev_E<double>(LevelData& lv) { return lv.E; }
+template <> float* lev_E<float>(LevelData& lv) { return lv.E32; }
+template <typename T> T* lev_RC(LevelData& lv);
+template <> double* lev_RC<double>(LevelData& lv) { return lv.RC; }
+template <> float* lev_RC<float>(LevelData& lv) { return lv.RC32; }
+template <typename T> T* scratch_X(fhmg_problem p);
+template <> double* scratch_X<double>(fhmg_problem p) { return p->Xs; }
+template <> float* scratch_X<float>(fhmg_problem p) { return p->Xs32; }
+
+// A smoother half-sweep / line-solve job on level l (shift of that level).
+template <typename T>
+fhmg::WalkArgsT<T> smooth_job(fhmg_problem p, int l, int kind, const Geo& g, long long nc, T* X, const T* B) {
   LevelData& lv = p->lev[l];
-  fhmg::WalkArgs a{};
+  fhmg::WalkArgsT<T> a{};
+  a.P = kind == K64 ? p->panel64.d : p->panel32.d;
   a.mode = fhmg::MODE_SMOOTH;
   a.geo = g;
   a.ncols = nc;
   a.X = X;
   a.B = B;
   a.OUT = nullptr;
-  a.Dinv = mixed ? (const void*)lv.Dinv32 : (const void*)lv.Dinv64;
-  a.ddiag = mixed ? lv.dinvdiag : nullptr;
+  a.Dinv = kind == K64 ? (const void*)lv.Dinv64 : (const void*)lv.Dinv32;
+  a.ddiag = kind == KSPLIT ? (const T*)lv.dinvdiag : nullptr;
   a.norm = nullptr;
-  return walk(p, mixed, a);
+  a.err = p->derr;
+  a.tile = tuned_tile(p, kind, fhmg::MODE_SMOOTH, nc);
+  return a;
 }
 
-// OUT = B - R~ X on nc compact columns (OUT may alias B or be NULL); optional max-norm.
-int walk_matvec(fhmg_problem p, bool mixed, long long nc, const double* X, const double* B, double* OUT,
-                unsigned long long* norm) {
-  fhmg::WalkArgs a{};
+// A product job: OUT = B - R~ X on nc compact columns (OUT may alias B or be NULL).
+template <typename T>
+fhmg::WalkArgsT<T> matvec_job(fhmg_problem p, int kind, long long nc, const T* X, const T* B, T* OUT,
+                              unsigned long long* norm) {
+  fhmg::WalkArgsT<T> a{};
+  a.P = kind == K64 ? p->panel64.d : p->panel32.d;
   a.mode = fhmg::MODE_MATVEC;
   a.geo = Geo{0, 0, 0, nc, 0.0};
   a.ncols = nc;
-  a.X = const_cast<double*>(X);
+  a.X = const_cast<T*>(X);
   a.B = B;
   a.OUT = OUT;
   a.Dinv = nullptr;
-  a.ddiag = mixed ? p->rdiag : nullptr;
+  a.ddiag = kind == KSPLIT ? (const T*)p->rdiag : nullptr;
   a.norm = norm;
-  return walk(p, mixed, a);
+  a.err = p->derr;
+  a.tile = tuned_tile(p, kind, fhmg::MODE_MATVEC, nc);
+  return a;
+}
+
+// Launches a list of jobs of one kind and mode on stream st: one persistent kernel per group of
+// up to kMaxJobs jobs with the same leaf size (the tile of each group's first job applies).
+int launch_jobs(cudaStream_t st, int kind, std::vector<fhmg::WalkArgsT<double>>& jobs, long long* counter) {
+  std::vector<fhmg::WalkArgsT<double>> live;
+  for (auto& j : jobs)
+    if (j.ncols > 0) live.push_back(j);
+  std::stable_sort(live.begin(), live.end(), [](const fhmg::WalkArgsT<double>& x, const fhmg::WalkArgsT<double>& y) {
+    return x.P.L < y.P.L;
+  });
+  size_t i = 0;
+  while (i < live.size()) {
+    size_t e = i;
+    while (e < live.size() && live[e].P.L == live[i].P.L && e - i < (size_t)fhmg::kMaxJobs) ++e;
+    std::string err;
+    int s = kind == KSPLIT ? fhmg::walk_launch_df(st, &live[i], (int)(e - i), &err, nullptr)
+                           : fhmg::walk_launch_dd(st, &live[i], (int)(e - i), &err, nullptr);
+    TRY(walk_status(s, err));
+    if (counter) ++*counter;
+    i = e;
+  }
+  return FHMG_OK;
+}
+
+int launch_jobs(cudaStream_t st, int, std::vector<fhmg::WalkArgsT<float>>& jobs, long long* counter) {
+  for (auto& j : jobs) {
+    if (j.ncols <= 0) continue;
+    std::string err;
+    TRY(walk_status(fhmg::walk_launch_ff(st, &j, 1, &err, nullptr), err));
+    if (counter) ++*counter;
+  }
+  return FHMG_OK;
+}
+
+template <typename T>
+int walk_smooth(fhmg_problem p, int l, int kind, const Geo& g, long long nc, T* X, const T* B) {
+  std::vector<fhmg::WalkArgsT<T>> j{smooth_job<T>(p, l, kind, g, nc, X, B)};
+  return launch_jobs(p->st, kind, j, &p->launches);
+}
+
+template <typename T>
+int walk_matvec(fhmg_problem p, int kind, long long nc, const T* X, const T* B, T* OUT, unsigned long long* norm) {
+  std::vector<fhmg::WalkArgsT<T>> j{matvec_job<T>(p, kind, nc, X, B, OUT, norm)};
+  return launch_jobs(p->st, kind, j, &p->launches);
 }
 
 // ---------------------------------------------------------------- driver steps
 
-int sweep(fhmg_problem p, int l, double* u, const double* F, bool mixed) {
+template <typename T>
+int sweep(fhmg_problem p, int l, T* u, const T* F, int kind) {
   LevelData& lv = p->lev[l];
   for (int colour = 0; colour < 2; ++colour) {
     const long long nc = fhmg::colour_count(p->dim, lv.N, colour);
@@ -230,40 +300,44 @@ int sweep(fhmg_problem p, int l, double* u, const double* F, bool mixed) {
     Geo g{p->dim, lv.N, colour, lv.npts, lv.inv_h2};
     const bool rec = p->profile && l == p->nlev - 1;
     if (rec) TRY(record_event(p));
-    TRY(walk_smooth(p, l, mixed, g, nc, u, F));
+    TRY(walk_smooth<T>(p, l, kind, g, nc, u, F));
     if (rec) TRY(record_event(p));
   }
   return FHMG_OK;
 }
 
 // rc = FW(F - A_h u) - R~ FW(u) on level l-1
-int restrict_defect(fhmg_problem p, int l, const double* u, const double* F, double* rc, bool mixed) {
+template <typename T>
+int restrict_defect(fhmg_problem p, int l, const T* u, const T* F, T* rc, int kind) {
   LevelData& lv = p->lev[l];
   LevelData& lc = p->lev[l - 1];
   const long long n = lc.npts * p->M;
-  fhmg::restrict_pre_kernel<double><<<blocks_for(n), 256, 0, p->st>>>(p->dim, lv.N, lv.inv_h2, p->M, u, F, p->Xs, rc);
+  T* xs = scratch_X<T>(p);
+  fhmg::restrict_pre_kernel<T><<<blocks_for(n), 256, 0, p->st>>>(p->dim, lv.N, lv.inv_h2, p->M, u, F, xs, rc);
   ++p->launches;
   CK(cudaGetLastError());
-  return walk_matvec(p, mixed, lc.npts, p->Xs, rc, rc, nullptr);
+  return walk_matvec<T>(p, kind, lc.npts, xs, rc, rc, nullptr);
 }
 
-int prolong_add(fhmg_problem p, int l, const double* e, double* u) {
+template <typename T>
+int prolong_add(fhmg_problem p, int l, const T* e, T* u) {
   const long long n = p->lev[l].npts * p->M;
-  fhmg::prolong_add_kernel<double><<<blocks_for(n), 256, 0, p->st>>>(p->dim, p->lev[l].N, p->M, e, u);
+  fhmg::prolong_add_kernel<T><<<blocks_for(n), 256, 0, p->st>>>(p->dim, p->lev[l].N, p->M, e, u);
   ++p->launches;
   CK(cudaGetLastError());
   return FHMG_OK;
 }
 
-int vcycle_rec(fhmg_problem p, int l, double* u, const double* F, int nu1, int nu2, bool mixed) {
-  if (l == 0) return sweep(p, 0, u, F, mixed);  // one interior point: the colour-0 solve is exact
-  for (int s = 0; s < nu1; ++s) TRY(sweep(p, l, u, F, mixed));
+template <typename T>
+int vcycle_rec(fhmg_problem p, int l, T* u, const T* F, int nu1, int nu2, int kind) {
+  if (l == 0) return sweep<T>(p, 0, u, F, kind);  // one interior point: the colour-0 solve is exact
+  for (int s = 0; s < nu1; ++s) TRY(sweep<T>(p, l, u, F, kind));
   LevelData& lc = p->lev[l - 1];
-  TRY(restrict_defect(p, l, u, F, lc.RC, mixed));
-  CK(cudaMemsetAsync(lc.E, 0, sizeof(double) * lc.npts * p->M, p->st));
-  TRY(vcycle_rec(p, l - 1, lc.E, lc.RC, nu1, nu2, mixed));
-  TRY(prolong_add(p, l, lc.E, u));
-  for (int s = 0; s < nu2; ++s) TRY(sweep(p, l, u, F, mixed));
+  TRY(restrict_defect<T>(p, l, u, F, lev_RC<T>(lc), kind));
+  CK(cudaMemsetAsync(lev_E<T>(lc), 0, sizeof(T) * lc.npts * p->M, p->st));
+  TRY(vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind));
+  TRY(prolong_add<T>(p, l, lev_E<T>(lc), u));
+  for (int s = 0; s < nu2; ++s) TRY(sweep<T>(p, l, u, F, kind));
   return FHMG_OK;
 }
 
@@ -292,14 +366,14 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
                                                                                   p->Xs, p->Rs);
     ++p->launches;
     CK(cudaGetLastError());
-    TRY(walk_matvec(p, false, nc, p->Xs, p->Rs, nullptr, p->dnorm));
+    TRY(walk_matvec<double>(p, K64, nc, p->Xs, p->Rs, nullptr, p->dnorm));
   } else {
     double* dst = R ? R : p->Rs;
     fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
                                                                                        u, F, nullptr, dst);
     ++p->launches;
     CK(cudaGetLastError());
-    TRY(walk_matvec(p, false, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
+    TRY(walk_matvec<double>(p, K64, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
   }
   return read_norm(p, out);
 }
@@ -341,7 +415,7 @@ int solve_fp64(fhmg_problem p, double* u, const double* F, int nu1, int nu2, dou
   r = r0;
   int k = 0;
   while (r > rtol * r0 && k < max_cycles) {
-    TRY(vcycle_rec(p, p->nlev - 1, u, F, nu1, nu2, false));
+    TRY(vcycle_rec<double>(p, p->nlev - 1, u, F, nu1, nu2, K64));
     TRY(fine_defect(p, u, F, nu2 > 0, nullptr, &r));
     ++k;
     if (!std::isfinite(r)) return fail(FHMG_ENAN, "residual became non-finite after %d cycles", k);
@@ -352,27 +426,233 @@ int solve_fp64(fhmg_problem p, double* u, const double* F, int nu1, int nu2, dou
   return FHMG_OK;
 }
 
-// Mixed path (defect correction): r = F - A u in FP64; p->inner V-cycles with FP32 H-matrix
-// products on A e = r from e = 0; u += e; repeat until ||r|| <= rtol ||r_0||.
+__global__ void to_float_kernel(const double* x, float* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void add_float_kernel(double* y, const float* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += (double)x[i];
+}
+
+__global__ void absmax_kernel(const double* x, long long n, unsigned long long* out) {
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = fabs(x[i]);
+    m = (a > m || a != a) ? a : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double b = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (b > m || b != b) ? b : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// max |x| over n device doubles (FP64, NaN propagates)
+int absmax(fhmg_problem p, const double* x, long long n, double* out) {
+  CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), p->st));
+  absmax_kernel<<<blocks_for(n), 256, 0, p->st>>>(x, n, p->dnorm);
+  ++p->launches;
+  CK(cudaGetLastError());
+  return read_norm(p, out);
+}
+
+// Inner storage of the mixed path: FP32 when the grid is well conditioned for it --
+// eps32 * cond(A_h) ~ 6e-8 * 4 (N+1)^2 / pi^2 <= 0.05 (the FP32 rounding of a correction then
+// perturbs the defect by at most ~5 %), otherwise FP64 storage with FP32 products.
+bool inner_fp32(fhmg_problem p) {
+  if (p->mixed_storage == 1) return false;
+  if (p->mixed_storage == 2) return true;
+  const double n1 = p->N + 1.0;
+  return 6e-8 * 4.0 * n1 * n1 / (M_PI * M_PI) <= 0.05;
+}
+
+// Mixed path (defect correction): r = F - A u in FP64; p->inner V-cycles on A e = r from e = 0
+// (FP32 storage and products, or FP64 storage with FP32 products); u += e; repeat until
+// ||r|| <= rtol ||r_0|| in FP64.
 int solve_mixed(fhmg_problem p, double* u, const double* F, int nu1, int nu2, double rtol, int max_cycles, int* kout,
                 double* r0out, double* rout) {
   const long long n = p->lev[p->nlev - 1].npts * p->M;
+  const bool f32 = inner_fp32(p);
   double r0, r;
-  TRY(fine_defect(p, u, F, false, p->Rs, &r0));
+  // a zero initial guess (the common case) has defect F: skip the FP64 product
+  double umax;
+  TRY(absmax(p, u, n, &umax));
+  if (umax == 0.0) {
+    TRY(absmax(p, F, n, &r0));
+    CK(cudaMemcpyAsync(p->Rs, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, p->st));
+  } else {
+    TRY(fine_defect(p, u, F, false, p->Rs, &r0));
+  }
   if (!std::isfinite(r0)) return fail(FHMG_ENAN, "initial residual is not finite");
   r = r0;
+  // FP32 storage limits one defect-correction step to ~1e-2 on these grids (two V-cycles reach
+  // it); FP64 storage with FP32 products converges like FP64 (four V-cycles ~ 1e-4)
+  const int inner = p->inner > 0 ? p->inner : (f32 ? 2 : 4);
   int k = 0;
   while (r > rtol * r0 && k < max_cycles) {
-    CK(cudaMemsetAsync(p->Ef, 0, sizeof(double) * n, p->st));
-    for (int j = 0; j < p->inner && k < max_cycles; ++j, ++k)
-      TRY(vcycle_rec(p, p->nlev - 1, p->Ef, p->Rs, nu1, nu2, true));
-    TRY(axpy(p, u, p->Ef, n, 1.0));
+    if (f32) {
+      to_float_kernel<<<blocks_for(n), 256, 0, p->st>>>(p->Rs, p->Rs32, n);
+      ++p->launches;
+      CK(cudaGetLastError());
+      CK(cudaMemsetAsync(p->Ef32, 0, sizeof(float) * n, p->st));
+      for (int j = 0; j < inner && k < max_cycles; ++j, ++k)
+        TRY(vcycle_rec<float>(p, p->nlev - 1, p->Ef32, p->Rs32, nu1, nu2, K32));
+      add_float_kernel<<<blocks_for(n), 256, 0, p->st>>>(u, p->Ef32, n);
+      ++p->launches;
+      CK(cudaGetLastError());
+    } else {
+      CK(cudaMemsetAsync(p->Ef, 0, sizeof(double) * n, p->st));
+      for (int j = 0; j < inner && k < max_cycles; ++j, ++k)
+        TRY(vcycle_rec<double>(p, p->nlev - 1, p->Ef, p->Rs, nu1, nu2, KSPLIT));
+      TRY(axpy(p, u, p->Ef, n, 1.0));
+    }
     TRY(fine_defect(p, u, F, false, p->Rs, &r));
     if (!std::isfinite(r)) return fail(FHMG_ENAN, "residual became non-finite after %d cycles", k);
   }
   *kout = k;
   *r0out = r0;
   *rout = r;
+  return FHMG_OK;
+}
+
+// ---------------------------------------------------------------- batched solves
+
+// One instance at one depth of a lockstep V-cycle.
+struct BLev {
+  fhmg_problem p;
+  int l;
+  double* u;
+  const double* F;
+};
+
+// Smoother sweeps of a set of instances: every colour is ONE launch over all of them.
+int batched_sweeps(cudaStream_t st, std::vector<BLev>& set, int nsweeps, int kind, long long* nl) {
+  for (int s = 0; s < nsweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      std::vector<fhmg::WalkArgsT<double>> jobs;
+      for (auto& b : set) {
+        LevelData& lv = b.p->lev[b.l];
+        const long long nc = fhmg::colour_count(b.p->dim, lv.N, colour);
+        jobs.push_back(smooth_job<double>(b.p, b.l, kind, Geo{b.p->dim, lv.N, colour, lv.npts, lv.inv_h2}, nc, b.u, b.F));
+      }
+      TRY(launch_jobs(st, kind, jobs, nl));
+    }
+  return FHMG_OK;
+}
+
+// V-cycle of every instance in lockstep by depth below its finest grid (instances with fewer
+// levels reach their coarsest grid earlier).  Capturable: no host synchronisation.
+int batched_vcycle(cudaStream_t st, std::vector<BLev> cur, int nu1, int nu2, int kind, long long* nl) {
+  std::vector<BLev> coarse, rest;
+  for (auto& b : cur) (b.l == 0 ? coarse : rest).push_back(b);
+  if (!coarse.empty()) TRY(batched_sweeps(st, coarse, 1, kind, nl));  // the one-point exact solve
+  if (rest.empty()) return FHMG_OK;
+  TRY(batched_sweeps(st, rest, nu1, kind, nl));
+  std::vector<fhmg::WalkArgsT<double>> jobs;
+  std::vector<BLev> next;
+  for (auto& b : rest) {
+    LevelData& lv = b.p->lev[b.l];
+    LevelData& lc = b.p->lev[b.l - 1];
+    const long long n = lc.npts * b.p->M;
+    fhmg::restrict_pre_kernel<double><<<blocks_for(n), 256, 0, st>>>(b.p->dim, lv.N, lv.inv_h2, b.p->M, b.u, b.F, b.p->Xs,
+                                                                      lc.RC);
+    CK(cudaGetLastError());
+    ++*nl;
+    jobs.push_back(matvec_job<double>(b.p, kind, lc.npts, b.p->Xs, lc.RC, lc.RC, nullptr));
+    CK(cudaMemsetAsync(lc.E, 0, sizeof(double) * n, st));
+    next.push_back(BLev{b.p, b.l - 1, lc.E, lc.RC});
+  }
+  TRY(launch_jobs(st, kind, jobs, nl));
+  TRY(batched_vcycle(st, next, nu1, nu2, kind, nl));
+  for (auto& b : rest) {
+    LevelData& lc = b.p->lev[b.l - 1];
+    const long long n = b.p->lev[b.l].npts * b.p->M;
+    fhmg::prolong_add_kernel<double><<<blocks_for(n), 256, 0, st>>>(b.p->dim, b.p->lev[b.l].N, b.p->M, lc.E, b.u);
+    CK(cudaGetLastError());
+    ++*nl;
+  }
+  return batched_sweeps(st, rest, nu2, kind, nl);
+}
+
+// FP64 defects of a set of instances (all points) into R_k, their max-norms into each dnorm;
+// one product launch for all of them.
+int batched_defects(cudaStream_t st, std::vector<BLev>& set, std::vector<double*>& R, long long* nl) {
+  std::vector<fhmg::WalkArgsT<double>> jobs;
+  for (size_t i = 0; i < set.size(); ++i) {
+    fhmg_problem p = set[i].p;
+    LevelData& lv = p->lev[p->nlev - 1];
+    CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), st));
+    fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
+                                                                                    set[i].u, set[i].F, nullptr, R[i]);
+    CK(cudaGetLastError());
+    ++*nl;
+    jobs.push_back(matvec_job<double>(p, K64, lv.npts, set[i].u, R[i], R[i], p->dnorm));
+  }
+  return launch_jobs(st, K64, jobs, nl);
+}
+
+// FP64 colour-0 defect norms (after completed sweeps) of a set of instances.
+int batched_colour0_norms(cudaStream_t st, std::vector<BLev>& set, long long* nl) {
+  std::vector<fhmg::WalkArgsT<double>> jobs;
+  for (auto& b : set) {
+    fhmg_problem p = b.p;
+    LevelData& lv = p->lev[p->nlev - 1];
+    const long long nc = fhmg::colour_count(p->dim, lv.N, 0);
+    CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), st));
+    fhmg::gather_defect_kernel<double><<<blocks_for(nc * p->M), 256, 0, st>>>(p->dim, lv.N, 0, lv.inv_h2, p->M, b.u, b.F,
+                                                                               p->Xs, p->Rs);
+    CK(cudaGetLastError());
+    ++*nl;
+    jobs.push_back(matvec_job<double>(p, K64, nc, p->Xs, p->Rs, nullptr, p->dnorm));
+  }
+  return launch_jobs(st, K64, jobs, nl);
+}
+
+int read_norms(cudaStream_t st, std::vector<BLev>& set, std::vector<double>& out) {
+  std::vector<unsigned long long> bits(set.size());
+  std::vector<int> errs(set.size());
+  for (size_t i = 0; i < set.size(); ++i) {
+    CK(cudaMemcpyAsync(&bits[i], set[i].p->dnorm, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&errs[i], set[i].p->derr, 4, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  out.resize(set.size());
+  for (size_t i = 0; i < set.size(); ++i) {
+    if (errs[i]) return fail(FHMG_ETIMEOUT, "a panel kernel gave up waiting on a shared-memory stage");
+    std::memcpy(&out[i], &bits[i], 8);
+  }
+  return FHMG_OK;
+}
+
+// A CUDA graph of one lockstep V-cycle of a fixed set of instances.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+int capture_cycle(cudaStream_t st, std::vector<BLev>& set, int nu1, int nu2, int kind, long long* nl, CycleGraph& g) {
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  // first run outside the capture: configures kernel attributes (shared-memory opt-in)
+  TRY(batched_vcycle(st, set, nu1, nu2, kind, nl));
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  long long dummy = 0;
+  int s = batched_vcycle(st, set, nu1, nu2, kind, &dummy);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (s != FHMG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(FHMG_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(FHMG_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
   return FHMG_OK;
 }
 
@@ -395,7 +675,7 @@ int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, 
                                                                                      u, F, nullptr, B);
   ++p->launches;
   CK(cudaGetLastError());
-  TRY(walk_matvec(p, false, lv.npts, u, B, nullptr, norm_word));
+  TRY(walk_matvec<double>(p, K64, lv.npts, u, B, nullptr, norm_word));
   unsigned long long bits = 0;
   int derr = 0;
   CK(cudaMemcpyAsync(&bits, norm_word, sizeof bits, cudaMemcpyDeviceToHost, p->st));
@@ -556,6 +836,10 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     if (l < nlev - 1) {
       if ((st = dalloc(p->allocs, &lv.E, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);
       if ((st = dalloc(p->allocs, &lv.RC, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);
+      if (mixed) {
+        if ((st = dalloc(p->allocs, &lv.E32, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);
+        if ((st = dalloc(p->allocs, &lv.RC32, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);
+      }
     }
   }
   const LevelData& fine = p->lev[nlev - 1];
@@ -563,7 +847,12 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   long long coarse = nlev > 1 ? p->lev[nlev - 2].npts : 1;
   if ((st = dalloc(p->allocs, &p->Xs, (size_t)std::max(c0, coarse) * M)) != FHMG_OK) return bail(st);
   if ((st = dalloc(p->allocs, &p->Rs, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
-  if (mixed && (st = dalloc(p->allocs, &p->Ef, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
+  if (mixed) {
+    if ((st = dalloc(p->allocs, &p->Ef, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
+    if ((st = dalloc(p->allocs, &p->Xs32, (size_t)std::max(c0, coarse) * M)) != FHMG_OK) return bail(st);
+    if ((st = dalloc(p->allocs, &p->Rs32, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
+    if ((st = dalloc(p->allocs, &p->Ef32, (size_t)fine.npts * M)) != FHMG_OK) return bail(st);
+  }
   const double* dm;
   if ((st = upload(p->allocs, h->host.dmm, &dm, nullptr)) != FHMG_OK) return bail(st);
   p->dmm = const_cast<double*>(dm);
@@ -574,12 +863,91 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   return FHMG_OK;
 }
 
-int fhmg_problem_autotune(fhmg_problem p) { return check_dims(p); }
+// Autotuner: for every walk the solver issues on this problem (smoother colours of every level,
+// products on the coarse columns of every restriction, the finest-grid defects), times each
+// column tile TC in {1, 2, 4, 8, 16, 32} that fits in shared memory (3 launches each, CUDA
+// events, on zeroed workspaces) and records the fastest; later launches use it.
+int fhmg_problem_autotune(fhmg_problem p) {
+  TRY(check_dims(p));
+  const int M = p->M;
+  const LevelData& fine = p->lev[p->nlev - 1];
+  CK(cudaMemsetAsync(p->Rs, 0, sizeof(double) * fine.npts * M, p->st));
+  CK(cudaMemsetAsync(p->Xs, 0, sizeof(double) * std::max(fhmg::colour_count(p->dim, p->N, 0),
+                                                         p->nlev > 1 ? p->lev[p->nlev - 2].npts : 1) * M, p->st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<int> kinds{K64};
+  if (p->prec == FHMG_MIXED_FP32) kinds.push_back(KSPLIT);
+  int st = FHMG_OK;
+  auto time_jobs = [&](int kind, fhmg::WalkArgsT<double> job, float* ms) -> int {
+    std::vector<fhmg::WalkArgsT<double>> v{job};
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) CK(cudaEventRecord(e0, p->st));
+      int s2 = launch_jobs(p->st, kind, v, nullptr);
+      if (s2 != FHMG_OK) return s2;
+    }
+    CK(cudaEventRecord(e1, p->st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    return FHMG_OK;
+  };
+  for (int kind : kinds) {
+    for (int l = 0; l < p->nlev && st == FHMG_OK; ++l) {
+      LevelData& lv = p->lev[l];
+      for (int mode = 0; mode < 2 && st == FHMG_OK; ++mode) {
+        std::vector<long long> cols;
+        if (mode == fhmg::MODE_SMOOTH) {
+          cols.push_back(fhmg::colour_count(p->dim, lv.N, 0));
+          cols.push_back(fhmg::colour_count(p->dim, lv.N, 1));
+        } else {
+          cols.push_back(lv.npts);  // restriction into this level / full finest defect
+          if (l == p->nlev - 1) cols.push_back(fhmg::colour_count(p->dim, lv.N, 0));
+        }
+        for (size_t ci = 0; ci < cols.size(); ++ci) {
+          const long long nc = cols[ci];
+          if (nc <= 0 || p->tune.count(std::make_pair(kind * 2 + mode, nc))) continue;
+          float best = 1e30f;
+          int best_tc = 0;
+          for (int tc = 1; tc <= 32; tc *= 2) {
+            fhmg::WalkArgsT<double> job =
+                mode == fhmg::MODE_SMOOTH
+                    ? smooth_job<double>(p, l, kind, Geo{p->dim, lv.N, (int)ci, lv.npts, lv.inv_h2}, nc, p->Rs, p->Rs)
+                    : matvec_job<double>(p, kind, nc, p->Xs, p->Rs, p->Rs, nullptr);
+            job.tile = tc;
+            float ms = 0.f;
+            int s2 = time_jobs(kind, job, &ms);
+            if (s2 == FHMG_EINVAL) continue;  // this tile does not fit
+            if (s2 != FHMG_OK) {
+              st = s2;
+              break;
+            }
+            if (ms < best) {
+              best = ms;
+              best_tc = tc;
+            }
+          }
+          if (best_tc) p->tune[std::make_pair(kind * 2 + mode, nc)] = best_tc;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
 
 int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles) {
   TRY(check_dims(p));
-  if (inner_cycles < 1) return fail(FHMG_EINVAL, "inner_cycles must be >= 1");
+  if (inner_cycles < 0) return fail(FHMG_EINVAL, "inner_cycles must be >= 0");
   p->inner = inner_cycles;
+  return FHMG_OK;
+}
+
+int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode) {
+  TRY(check_dims(p));
+  if (mode < 0 || mode > 2) return fail(FHMG_EINVAL, "mixed storage mode must be 0, 1 or 2");
+  p->mixed_storage = mode;
   return FHMG_OK;
 }
 
@@ -612,14 +980,14 @@ int fhmg_line_solve(fhmg_problem p, int level, double* X, const double* B, long 
   if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
   if (!X || !B || ncols < 0) return fail(FHMG_EINVAL, "bad arrays");
   Geo g{0, 0, 0, ncols, 0.0};
-  return walk_smooth(p, level, false, g, ncols, X, B);
+  return walk_smooth<double>(p, level, K64, g, ncols, X, B);
 }
 
 int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
   TRY(check_dims(p));
   if (!X || !Y || ncols < 0 || X == Y) return fail(FHMG_EINVAL, "bad arrays");
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
-  TRY(walk_matvec(p, false, ncols, X, Y, Y, nullptr));
+  TRY(walk_matvec<double>(p, K64, ncols, X, Y, Y, nullptr));
   scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
   ++p->launches;
   CK(cudaGetLastError());
@@ -629,7 +997,7 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
 int fhmg_smooth(fhmg_problem p, double* u, const double* F, int nsweeps) {
   TRY(check_dims(p));
   if (!u || !F || nsweeps < 0) return fail(FHMG_EINVAL, "bad arguments");
-  for (int s = 0; s < nsweeps; ++s) TRY(sweep(p, p->nlev - 1, u, F, false));
+  for (int s = 0; s < nsweeps; ++s) TRY(sweep<double>(p, p->nlev - 1, u, F, K64));
   return FHMG_OK;
 }
 
@@ -646,14 +1014,14 @@ int fhmg_restrict_residual(fhmg_problem p, const double* u, const double* F, dou
   TRY(check_dims(p));
   if (p->nlev < 2) return fail(FHMG_EINVAL, "no coarser grid");
   if (!u || !F || !rc) return fail(FHMG_EINVAL, "bad arrays");
-  return restrict_defect(p, p->nlev - 1, u, F, rc, false);
+  return restrict_defect<double>(p, p->nlev - 1, u, F, rc, K64);
 }
 
 int fhmg_prolong_correct(fhmg_problem p, double* u, const double* e) {
   TRY(check_dims(p));
   if (p->nlev < 2) return fail(FHMG_EINVAL, "no coarser grid");
   if (!u || !e) return fail(FHMG_EINVAL, "bad arrays");
-  return prolong_add(p, p->nlev - 1, e, u);
+  return prolong_add<double>(p, p->nlev - 1, e, u);
 }
 
 int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int nu1, int nu2) {
@@ -661,7 +1029,7 @@ int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int
   if (!u || nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0) return fail(FHMG_EINVAL, "bad arguments");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
-  return vcycle_rec(p, p->nlev - 1, u, F, nu1, nu2, false);
+  return vcycle_rec<double>(p, p->nlev - 1, u, F, nu1, nu2, K64);
 }
 
 int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const double* g, double* out) {
@@ -711,6 +1079,161 @@ int fhmg_solve_host(fhmg_problem p, double* u_host, const double* f_host, const 
   CK(cudaMemcpyAsync(u_host, p->hu, n * sizeof(double), cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
   return st;
+}
+
+int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f, int nu1, int nu2, double rtol,
+                       int max_cycles, int* cycles_out, double* relres_out) {
+  if (n < 1 || n > 4096 || !probs || !u || !f) return fail(FHMG_EINVAL, "bad batch");
+  if (nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0 || !(rtol >= 0) || max_cycles < 0) return fail(FHMG_EINVAL, "bad arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!probs[i] || !u[i] || !f[i]) return fail(FHMG_EINVAL, "null problem or array in the batch");
+    if (probs[i]->prec != probs[0]->prec) return fail(FHMG_EINVAL, "all problems of a batch must share the precision");
+  }
+  const bool mixed = probs[0]->prec == FHMG_MIXED_FP32;
+  const int kind = mixed ? KSPLIT : K64;  // the batched mixed path keeps FP64 storage (valid for every N)
+  cudaStream_t st;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  struct Cleanup {
+    cudaStream_t s;
+    cudaEvent_t e;
+    ~Cleanup() {
+      cudaEventDestroy(e);
+      cudaStreamDestroy(s);
+    }
+  } cleanup{st, ev};
+  for (int i = 0; i < n; ++i) {  // order after the callers' streams
+    CK(cudaEventRecord(ev, probs[i]->st));
+    CK(cudaStreamWaitEvent(st, ev, 0));
+  }
+  long long nl = 0;
+  std::vector<BLev> set(n);
+  std::vector<double*> R(n);
+  for (int i = 0; i < n; ++i) {
+    set[i] = BLev{probs[i], probs[i]->nlev - 1, u[i], f[i]};
+    R[i] = probs[i]->Rs;
+  }
+  std::vector<double> r0, r;
+  TRY(batched_defects(st, set, R, &nl));
+  TRY(read_norms(st, set, r0));
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(r0[i])) return fail(FHMG_ENAN, "initial residual of instance %d is not finite", i);
+  r = r0;
+  std::vector<int> cyc(n, 0);
+  auto active_list = [&]() {
+    std::vector<int> a;
+    for (int i = 0; i < n; ++i)
+      if (r[i] > rtol * r0[i] && cyc[i] < max_cycles) a.push_back(i);
+    return a;
+  };
+  std::vector<int> act = active_list();
+  CycleGraph graph;
+  std::vector<int> graph_set;
+  while (!act.empty()) {
+    std::vector<BLev> sub;
+    for (int i : act)
+      sub.push_back(mixed ? BLev{probs[i], probs[i]->nlev - 1, probs[i]->Ef, probs[i]->Rs} : set[i]);
+    const int ncyc = mixed ? (probs[0]->inner > 0 ? probs[0]->inner : 4) : 1;
+    if (mixed)
+      for (int i : act)
+        CK(cudaMemsetAsync(probs[i]->Ef, 0, sizeof(double) * probs[i]->lev[probs[i]->nlev - 1].npts * probs[i]->M, st));
+    for (int c = 0; c < ncyc; ++c) {
+      if (graph_set != act) {
+        TRY(capture_cycle(st, sub, nu1, nu2, kind, &nl, graph));  // runs this cycle, then captures it
+        graph_set = act;
+      } else {
+        CK(cudaGraphLaunch(graph.exec, st));
+        ++nl;
+      }
+    }
+    for (int i : act) cyc[i] += ncyc;
+    std::vector<BLev> chk;
+    for (int i : act) chk.push_back(set[i]);
+    std::vector<double> rn;
+    if (mixed) {
+      for (int i : act) {
+        const long long ne = probs[i]->lev[probs[i]->nlev - 1].npts * probs[i]->M;
+        axpy_kernel<<<blocks_for(ne), 256, 0, st>>>(u[i], probs[i]->Ef, ne, 1.0);
+        CK(cudaGetLastError());
+        ++nl;
+      }
+      std::vector<double*> Ra;
+      for (int i : act) Ra.push_back(probs[i]->Rs);
+      TRY(batched_defects(st, chk, Ra, &nl));
+    } else if (nu2 > 0) {
+      TRY(batched_colour0_norms(st, chk, &nl));
+    } else {
+      std::vector<double*> Ra;
+      for (int i : act) Ra.push_back(probs[i]->Rs);
+      TRY(batched_defects(st, chk, Ra, &nl));
+    }
+    TRY(read_norms(st, chk, rn));
+    for (size_t k = 0; k < act.size(); ++k) {
+      if (!std::isfinite(rn[k])) return fail(FHMG_ENAN, "residual of instance %d became non-finite", act[k]);
+      r[act[k]] = rn[k];
+    }
+    act = active_list();
+  }
+  for (int i = 0; i < n; ++i) {  // the callers' streams wait for the batch
+    probs[i]->launches += nl / n;
+    if (cycles_out) cycles_out[i] = cyc[i];
+    if (relres_out) relres_out[i] = r0[i] > 0 ? r[i] / r0[i] : 0.0;
+  }
+  CK(cudaEventRecord(ev, st));
+  for (int i = 0; i < n; ++i) CK(cudaStreamWaitEvent(probs[i]->st, ev, 0));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i)
+    if (r[i] > rtol * r0[i]) return fail(FHMG_ENOTCONV, "instance %d: relative residual %.3e after %d cycles", i,
+                                         r0[i] > 0 ? r[i] / r0[i] : 0.0, cyc[i]);
+  return FHMG_OK;
+}
+
+int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, int dim, int N, double Lx, int prec,
+                       void* stream, int* best_leaf, double* best_ms) {
+  if (!best_leaf) return fail(FHMG_EINVAL, "best_leaf is NULL");
+  double best = 1e300;
+  int bl = 0;
+  for (int leaf : {32, 64}) {
+    if (leaf > M) continue;
+    fhmg_hmatrix h = nullptr;
+    if (fhmg_build_hmatrix(alpha, gamma, T, M, leaf, 0, tol, &h) != FHMG_OK) continue;
+    fhmg_problem p = nullptr;
+    int s = fhmg_problem_create(h, dim, N, Lx, prec, stream, &p);
+    if (s != FHMG_OK) {
+      fhmg_hmatrix_destroy(h);
+      return s;
+    }
+    s = fhmg_problem_autotune(p);
+    // time one V-cycle (after a warm-up cycle) on the zeroed workspace: iterate and right-hand
+    // side both in Rs (fine-grid size; values do not change the cost)
+    const LevelData& fine = p->lev[p->nlev - 1];
+    const int kind = p->prec == FHMG_MIXED_FP32 ? KSPLIT : K64;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    if (s == FHMG_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+      cudaMemsetAsync(p->Rs, 0, sizeof(double) * fine.npts * p->M, p->st);
+      s = vcycle_rec<double>(p, p->nlev - 1, p->Rs, p->Rs, 1, 1, kind);
+      cudaEventRecord(e0, p->st);
+      if (s == FHMG_OK) s = vcycle_rec<double>(p, p->nlev - 1, p->Rs, p->Rs, 1, 1, kind);
+      cudaEventRecord(e1, p->st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    fhmg_problem_destroy(p);
+    fhmg_hmatrix_destroy(h);
+    if (s != FHMG_OK) return s;
+    if (ms < best) {
+      best = ms;
+      bl = leaf;
+    }
+  }
+  if (!bl) return fail(FHMG_EINVAL, "no leaf size could be built for M = %d", M);
+  *best_leaf = bl;
+  if (best_ms) *best_ms = best;
+  return FHMG_OK;
 }
 
 }  // extern "C"

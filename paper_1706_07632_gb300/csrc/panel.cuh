@@ -108,23 +108,55 @@ __host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, 
   return s;
 }
 
-// MODE_SMOOTH: X (at geometry positions) = (R~ + s I)^{-1} (F + neighbour sum / h^2);
-//   Bsrc = F; Dinv = the level's inverted diagonal leaves (streamed as the DIAG chunks).
-// MODE_MATVEC: OUT = B - R~ X on compact columns (ld = geo.ld); OUT may alias B or be NULL;
-//   norm != NULL folds max |OUT| into *norm (bit pattern of a non-negative double).
-// ddiag (mixed path only): the FP64 diagonal of the streamed DIAG blocks, nb x L; the
-//   streamed blocks' own diagonal is then skipped and the diagonal term is applied in T.
-// err: set to 1 if an mbarrier wait exceeds kSpinLimit (the kernel then returns early).
+// One walk job: one instance (H-matrix, grid, arrays) of a batched launch.
+//   MODE_SMOOTH: X (at geometry positions) = (R~ + s I)^{-1} (F + neighbour sum / h^2);
+//     B = F; Dinv = the level's inverted diagonal leaves (streamed as the DIAG chunks).
+//   MODE_MATVEC: OUT = B - R~ X on compact columns (ld = geo.ld); OUT may alias B or be NULL;
+//     norm != NULL folds max |OUT| into *norm (bit pattern of a non-negative double).
+//   ddiag (FP64-storage mixed path only): the FP64 diagonal of the streamed DIAG blocks, nb x L;
+//     the streamed blocks' own diagonal is then skipped and the diagonal term applied in T.
+constexpr int kMaxJobs = 64;
+
+template <typename T, typename TM>
+struct WalkJob {
+  PanelDev P;       // the job's chunk stream (P.ns unused)
+  Geo geo;
+  long long ncols;
+  long long tile0;  // first global tile of the job
+  T* X;
+  const T* B;
+  T* OUT;
+  const TM* Dinv;
+  const T* ddiag;
+  unsigned long long* norm;
+};
+
+// A launch: up to kMaxJobs jobs with the same leaf size, column tile and mode, passed by value
+// (kernel parameter space).  The shared-memory layout uses the maxima over the jobs.
+template <typename T, typename TM>
+struct WalkBatch {
+  int njobs;
+  int ns, pool, W, slot_bytes;
+  long long ntiles;  // tiles over all jobs
+  int* err;          // set to 1 if an mbarrier wait exceeds kSpinLimit (the kernel then returns)
+  WalkJob<T, TM> job[kMaxJobs];
+};
+
+template <typename T, typename TM>
+__device__ __forceinline__ int job_of(const WalkBatch<T, TM>& B, long long g) {
+  int j = 0;
+  while (j + 1 < B.njobs && B.job[j + 1].tile0 <= g) ++j;
+  return j;
+}
+
 template <typename T, typename TM, int L, int TC, int MODE, int NT_>
-__global__ void __launch_bounds__(NT_)
-hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT, const TM* Dinv,
-              const T* ddiag, unsigned long long* norm, int* err) {
+__global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ WalkBatch<T, TM> B) {
   using TL = PTile<L, TC, NT_>;
   constexpr int NT = TL::NT, Q = TL::Q, RG = TL::RG, S = TL::S;
   constexpr int KS = L / S;
   constexpr int NA = KS >= 4 ? 4 : KS;
   extern __shared__ __align__(16) unsigned char sm[];
-  const PanelSmem lay = panel_smem(L, TC, P.pool, P.W, P.slot_bytes, P.ns, sizeof(T), sizeof(TM));
+  const PanelSmem lay = panel_smem(L, TC, B.pool, B.W, B.slot_bytes, B.ns, sizeof(T), sizeof(TM));
   unsigned char* slots = sm;
   T* ys = reinterpret_cast<T*>(sm + lay.ys);     // y / x of the current leaf (T)
   TM* ysm = reinterpret_cast<TM*>(sm + lay.ysm);  // the same in TM, converted once per leaf
@@ -137,23 +169,30 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
   const int cl = t % TC;
   const int sp = (t / TC) % S;
   const int rg = t / (TC * S);
-  const long long ld = geo.ld;
-  const T inv_h2 = (T)geo.inv_h2;
-  const int nch = __ldg(P.cptr + P.nb);
-  const long long ntiles = (ncols + TC - 1) / TC;
-  const long long my_tiles = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long total = my_tiles * nch;
-  const int ns = P.ns;
+  const int ns = B.ns;
+  const int W = B.W;
 
-  auto issue = [&](long long pos) {
-    const int c = (int)(pos % nch);
-    const int4 cd = __ldg(P.chunks + c);
+  // producer cursor (thread 0): the next (tile, chunk) to stage, in consumption order
+  long long pg = blockIdx.x;
+  int pj = pg < B.ntiles ? job_of(B, pg) : 0;
+  int pc = 0;
+  long long issued = 0;
+  auto issue_next = [&]() {
+    if (pg >= B.ntiles) return;
+    const WalkJob<T, TM>& J = B.job[pj];
+    const int4 cd = __ldg(J.P.chunks + pc);
     const int type = cd.x & 15;
     const void* src = (MODE == MODE_SMOOTH && type == PK_DIAG)
-                          ? (const void*)(Dinv + (long long)cd.y * L * L)
-                          : (const void*)(P.pkg + 16LL * (long long)cd.w);
-    const int slot = (int)(pos % ns);
-    bulk_load(slots + (size_t)slot * P.slot_bytes, src, (uint32_t)cd.z, bar + slot);
+                          ? (const void*)(J.Dinv + (long long)cd.y * L * L)
+                          : (const void*)(J.P.pkg + 16LL * (long long)cd.w);
+    const int slot = (int)(issued % ns);
+    bulk_load(slots + (size_t)slot * B.slot_bytes, src, (uint32_t)cd.z, bar + slot);
+    ++issued;
+    if (++pc == __ldg(J.P.cptr + J.P.nb)) {
+      pc = 0;
+      pg += gridDim.x;
+      if (pg < B.ntiles) pj = job_of(B, pg);
+    }
   };
 
   if (t == 0) {
@@ -162,32 +201,36 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (t == 0) {
-    for (long long s = 0; s < ns && s < total; ++s) issue(s);
-  }
+  if (t == 0)
+    for (int s = 0; s < ns; ++s) issue_next();
 
-  double local_max = 0.0;
   long long pos = 0;
-  for (long long lt = 0; lt < my_tiles; ++lt) {
-    const long long tile = blockIdx.x + lt * gridDim.x;
-    const long long cg = tile * TC + cl;
-    const bool valid = cg < ncols;
+  for (long long g = blockIdx.x; g < B.ntiles; g += gridDim.x) {
+    const WalkJob<T, TM>& J = B.job[job_of(B, g)];
+    const long long cg = (g - J.tile0) * TC + cl;
+    const bool valid = cg < J.ncols;
+    const long long ld = J.geo.ld;
+    const T inv_h2 = (T)J.geo.inv_h2;
+    T* X = J.X;
+    const T* Bsrc = J.B;
+    const int nb = J.P.nb;
     long long p = 0;
     long long nbr[4] = {-1, -1, -1, -1};
     if (valid) {
-      if (MODE == MODE_SMOOTH && geo.dim > 0) {
+      if (MODE == MODE_SMOOTH && J.geo.dim > 0) {
         int iy, ix;
-        p = colour_pos(geo.dim, geo.N, geo.colour, cg, &iy, &ix);
+        p = colour_pos(J.geo.dim, J.geo.N, J.geo.colour, cg, &iy, &ix);
         nbr[0] = ix > 0 ? p - 1 : -1;
-        nbr[1] = ix < geo.N - 1 ? p + 1 : -1;
-        if (geo.dim == 2) {
-          nbr[2] = iy > 0 ? p - geo.N : -1;
-          nbr[3] = iy < geo.N - 1 ? p + geo.N : -1;
+        nbr[1] = ix < J.geo.N - 1 ? p + 1 : -1;
+        if (J.geo.dim == 2) {
+          nbr[2] = iy > 0 ? p - J.geo.N : -1;
+          nbr[3] = iy < J.geo.N - 1 ? p + J.geo.N : -1;
         }
       } else {
         p = cg;
       }
     }
+    double local_max = 0.0;
     // right-hand side (and, for the product, the x tile) of the next leaf, prefetched
     T bn[Q], xn[Q];
     auto load_rhs = [&](int leaf) {
@@ -195,7 +238,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
       for (int q = 0; q < Q; ++q) {
         const int r = rg + RG * q;
         T b = 0, x = 0;
-        if (valid && sp == 0 && leaf < P.nb) {
+        if (valid && sp == 0 && leaf < nb) {
           const long long base = (long long)(leaf * L + r) * ld;
           b = Bsrc[base + p];
           if (MODE == MODE_SMOOTH) {
@@ -214,33 +257,32 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
     };
     load_rhs(0);
 
-    for (int i = 0; i < P.nb; ++i) {
+    for (int i = 0; i < nb; ++i) {
       T acc[Q];
       TM part[Q][NA];
+      T xcur[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         acc[q] = bn[q];
+        xcur[q] = xn[q];
 #pragma unroll
         for (int a = 0; a < NA; ++a) part[q][a] = 0;
       }
-      T xcur[Q];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) xcur[q] = xn[q];
-      const int c1 = __ldg(P.cptr + i + 1);
-      for (int c = __ldg(P.cptr + i); c < c1; ++c, ++pos) {
+      const int c1 = __ldg(J.P.cptr + i + 1);
+      for (int c = __ldg(J.P.cptr + i); c < c1; ++c, ++pos) {
         const int slot = (int)(pos % ns);
         if (!mbar_wait(bar + slot, (uint32_t)((pos / ns) & 1))) {
           *sflag = 1;
-          atomicExch(err, 1);
+          atomicExch(B.err, 1);
         }
-        const int4 cd = __ldg(P.chunks + c);
+        const int4 cd = __ldg(J.P.chunks + c);
         const int type = cd.x & 15, cnt = cd.x >> 4;
-        const unsigned char* buf = slots + (size_t)slot * P.slot_bytes;
+        const unsigned char* buf = slots + (size_t)slot * B.slot_bytes;
         if (type == PK_DENSE) {
           const TM* D = reinterpret_cast<const TM*>(buf);
           const int j = cd.y;
-          if (i - j < P.W) {
-            const TM* xr = ring + (size_t)(j % P.W) * L * TC;
+          if (i - j < W) {
+            const TM* xr = ring + (size_t)(j % W) * L * TC;
 #pragma unroll
             for (int kk = 0; kk < KS; ++kk) {
               const int k = sp + kk * S;
@@ -270,6 +312,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
           }
         } else if (type == PK_DIAG) {
           const TM* Dd = reinterpret_cast<const TM*>(buf);
+          const T* ddiag = J.ddiag;
 #pragma unroll
           for (int q = 0; q < Q; ++q) {
             TM s = part[q][0];
@@ -277,7 +320,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
             for (int a = 1; a < NA; ++a) s += part[q][a];
             acc[q] = reduce_splits<T, TC, S>(acc[q] - (T)s);
           }
-          TM* xr_i = ring + (size_t)(i % P.W) * L * TC;
+          TM* xr_i = ring + (size_t)(i % W) * L * TC;
           if (MODE == MODE_SMOOTH) {
             if (sp == 0) {
 #pragma unroll
@@ -345,7 +388,7 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
               T o = acc[q] - reduce_splits<T, TC, S>((T)s1);
               if (ddiag) o -= ddiag[(long long)i * L + r] * ys[r * TC + cl];
               if (valid && sp == 0) {
-                if (OUT) OUT[(long long)(i * L + r) * ld + p] = o;
+                if (J.OUT) J.OUT[(long long)(i * L + r) * ld + p] = o;
                 const double av = fabs((double)o);
                 local_max = (av > local_max || av != av) ? av : local_max;
               }
@@ -358,9 +401,9 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
           const int O = cnt * TC;
           int Sv = 32;
           while (Sv > 1 && Sv * O > NT) Sv >>= 1;
-          const int g = t / Sv, sv = t % Sv, G = NT / Sv;
+          const int gq = t / Sv, sv = t % Sv, G = NT / Sv;
           for (int base = 0; base < O; base += G) {
-            const int o = base + g;
+            const int o = base + gq;
             TM s = 0;
             if (o < O) {
               const int kk = o / TC, cc = o % TC;
@@ -379,23 +422,22 @@ hpanel_kernel(PanelDev P, Geo geo, long long ncols, T* X, const T* Bsrc, T* OUT,
         if (*sflag) {
           // drain (bounded) the copies still in flight, then leave
           if (t == 0)
-            for (long long q2 = pos + 1; q2 < total && q2 < pos + ns; ++q2)
-              mbar_wait(bar + (int)(q2 % ns), (uint32_t)((q2 / ns) & 1));
+            for (long long q2 = pos + 1; q2 < issued; ++q2) mbar_wait(bar + (int)(q2 % ns), (uint32_t)((q2 / ns) & 1));
           return;
         }
-        if (t == 0 && pos + ns < total) {
+        if (t == 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue(pos + ns);
+          issue_next();
         }
       }
     }
-  }
-  if (MODE == MODE_MATVEC && norm != nullptr) {
-    for (int o = 16; o > 0; o >>= 1) {
-      const double other = __shfl_xor_sync(0xffffffffu, local_max, o);
-      local_max = (other > local_max || other != other) ? other : local_max;
+    if (MODE == MODE_MATVEC && J.norm != nullptr) {
+      for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, local_max, o);
+        local_max = (other > local_max || other != other) ? other : local_max;
+      }
+      if ((t & 31) == 0) atomicMax(J.norm, (unsigned long long)__double_as_longlong(local_max));
     }
-    if ((t & 31) == 0) atomicMax(norm, (unsigned long long)__double_as_longlong(local_max));
   }
 }
 

@@ -7,22 +7,28 @@
 
 namespace fhmg {
 
-struct WalkArgs {
+// One walk job (one instance).
+template <typename T>
+struct WalkArgsT {
   PanelDev P;                  // ns is chosen by the launcher
-  int mode;                    // MODE_SMOOTH / MODE_MATVEC
+  int mode;                    // MODE_SMOOTH / MODE_MATVEC (the same for every job of a launch)
   Geo geo;
   long long ncols;
-  double* X;
-  const double* B;
-  double* OUT;
+  T* X;
+  const T* B;
+  T* OUT;
   const void* Dinv;            // TM*, level inverses (smoother)
-  const double* ddiag;         // mixed path only
+  const T* ddiag;              // FP64-storage mixed path only
   unsigned long long* norm;
-  int* err;                    // device error word (bounded-wait timeout)
-  int tile;                    // 0: automatic, else the column tile TC
+  int* err;                    // device error word (bounded-wait timeout); the first job's is used
+  int tile;                    // 0: automatic, else the column tile TC (the first job's is used)
 };
+using WalkArgs = WalkArgsT<double>;
 
-int walk_launch_dd(cudaStream_t st, const WalkArgs& a, std::string* err, int* tile_used);
-int walk_launch_df(cudaStream_t st, const WalkArgs& a, std::string* err, int* tile_used);
+// Launches njobs (1..kMaxJobs) jobs with the same leaf size and mode as one persistent kernel.
+// dd: FP64 storage, FP64 products; df: FP64 storage, FP32 products; ff: FP32 storage and products.
+int walk_launch_dd(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
+int walk_launch_df(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
+int walk_launch_ff(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std::string* err, int* tile_used);
 
 }  // namespace fhmg

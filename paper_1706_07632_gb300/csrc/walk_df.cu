@@ -4,8 +4,8 @@
 #include "walk_impl.cuh"
 
 namespace fhmg {
-int walk_launch_df(cudaStream_t st, const WalkArgs& a, std::string* err, int* tile_used) {
-  if (a.mode == MODE_SMOOTH) return panel_dispatch<float, MODE_SMOOTH>(st, a, err, tile_used);
-  return panel_dispatch<float, MODE_MATVEC>(st, a, err, tile_used);
+int walk_launch_df(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used) {
+  if (jobs[0].mode == MODE_SMOOTH) return panel_dispatch<double, float, MODE_SMOOTH>(st, jobs, njobs, err, tile_used);
+  return panel_dispatch<double, float, MODE_MATVEC>(st, jobs, njobs, err, tile_used);
 }
 }  // namespace fhmg

@@ -1,6 +1,7 @@
 // Template dispatch of hpanel_kernel over (leaf, column tile); included by the per-precision
 // translation units.
 #pragma once
+#include <algorithm>
 #include <string>
 
 #include "walk.h"
@@ -16,15 +17,15 @@ inline int panel_slots(int slot_bytes) {
   return ns < 2 ? 2 : (ns > 16 ? 16 : ns);
 }
 
-template <typename TM>
-size_t panel_bytes(const PanelDev& P, int L, int TC) {
-  return panel_smem(L, TC, P.pool, P.W, P.slot_bytes, P.ns, sizeof(double), sizeof(TM)).total;
+template <typename T, typename TM>
+size_t panel_bytes(int L, int TC, int pool, int W, int slot_bytes, int ns) {
+  return panel_smem(L, TC, pool, W, slot_bytes, ns, sizeof(T), sizeof(TM)).total;
 }
 
-template <typename TM, int L, int TC, int MODE>
-int panel_launch_t(cudaStream_t st, const WalkArgs& a, PanelDev P, std::string* err) {
-  auto kern = hpanel_kernel<double, TM, L, TC, MODE, kPanelThreads>;
-  const size_t smem = panel_bytes<TM>(P, L, TC);
+template <typename T, typename TM, int L, int TC, int MODE>
+int panel_launch_t(cudaStream_t st, const WalkBatch<T, TM>& B, std::string* err) {
+  auto kern = hpanel_kernel<T, TM, L, TC, MODE, kPanelThreads>;
+  const size_t smem = panel_bytes<T, TM>(L, TC, B.pool, B.W, B.slot_bytes, B.ns);
   static size_t configured = 48 * 1024;
   static size_t occ_smem = 0;
   static int occ = 1;
@@ -42,11 +43,9 @@ int panel_launch_t(cudaStream_t st, const WalkArgs& a, PanelDev P, std::string* 
     occ = o;
     occ_smem = smem;
   }
-  const long long ntiles = (a.ncols + TC - 1) / TC;
-  if (ntiles <= 0) return 0;
-  long long grid = std::min<long long>(ntiles, (long long)kPanelSMs * occ);
-  kern<<<(unsigned)grid, kPanelThreads, smem, st>>>(P, a.geo, a.ncols, a.X, a.B, a.OUT, (const TM*)a.Dinv, a.ddiag,
-                                                    a.norm, a.err);
+  if (B.ntiles <= 0) return 0;
+  const long long grid = std::min<long long>(B.ntiles, (long long)kPanelSMs * occ);
+  kern<<<(unsigned)grid, kPanelThreads, smem, st>>>(B);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("panel launch: ") + cudaGetErrorString(e);
@@ -58,28 +57,68 @@ int panel_launch_t(cudaStream_t st, const WalkArgs& a, PanelDev P, std::string* 
 // Column tile: the largest TC whose tiles still cover every SM (persistent CTAs reuse each
 // staged chunk for all TC columns), TC = 1 when there are fewer columns than SMs; shrunk until
 // the shared-memory layout fits.
-template <typename TM>
-int panel_pick(const PanelDev& P, int L, long long ncols) {
+template <typename T, typename TM>
+int panel_pick(int L, int pool, int W, int slot_bytes, int ns, long long ncols) {
   const int tcmax = (L == 64 && sizeof(TM) == 8) ? 16 : 32;  // FP64 leaf-64 tiles of 32 spill
   int tc = 1;
   while (tc < tcmax && (ncols + 2 * tc - 1) / (2 * tc) >= kPanelSMs) tc *= 2;
-  while (tc > 1 && panel_bytes<TM>(P, L, tc) > kPanelSmemCap) tc /= 2;
+  while (tc > 1 && panel_bytes<T, TM>(L, tc, pool, W, slot_bytes, ns) > kPanelSmemCap) tc /= 2;
   return tc;
 }
 
-template <typename TM, int MODE>
-int panel_dispatch(cudaStream_t st, const WalkArgs& a, std::string* err, int* tile_used) {
-  PanelDev P = a.P;
-  P.ns = panel_slots(P.slot_bytes);
-  const int L = P.L;
-  const int TC = a.tile ? a.tile : panel_pick<TM>(P, L, a.ncols);
+template <typename T, typename TM, int MODE>
+int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::string* err, int* tile_used) {
+  if (njobs < 1 || njobs > kMaxJobs) {
+    *err = "walk launch needs 1.." + std::to_string(kMaxJobs) + " jobs";
+    return 2;
+  }
+  const int L = jobs[0].P.L;
+  int pool = 0, W = 1, slot = 16;
+  long long cols = 0;
+  for (int j = 0; j < njobs; ++j) {
+    if (jobs[j].P.L != L) {
+      *err = "jobs of one walk launch must share the leaf size";
+      return 2;
+    }
+    pool = std::max(pool, jobs[j].P.pool);
+    W = std::max(W, jobs[j].P.W);
+    slot = std::max(slot, jobs[j].P.slot_bytes);
+    cols = std::max(cols, jobs[j].ncols);
+  }
+  const int ns = panel_slots(slot);
+  long long total_cols = 0;
+  for (int j = 0; j < njobs; ++j) total_cols += jobs[j].ncols;
+  const int TC = jobs[0].tile ? jobs[0].tile : panel_pick<T, TM>(L, pool, W, slot, ns, total_cols);
   if (tile_used) *tile_used = TC;
-  if (panel_bytes<TM>(P, L, TC) > 227 * 1024) {
+  if (panel_bytes<T, TM>(L, TC, pool, W, slot, ns) > 227 * 1024) {
     *err = "panel shared memory exceeds 227 KB";
     return 2;
   }
+  WalkBatch<T, TM> B;
+  B.njobs = njobs;
+  B.ns = ns;
+  B.pool = pool;
+  B.W = W;
+  B.slot_bytes = slot;
+  B.err = jobs[0].err;
+  long long tiles = 0;
+  for (int j = 0; j < njobs; ++j) {
+    WalkJob<T, TM>& J = B.job[j];
+    J.P = jobs[j].P;
+    J.geo = jobs[j].geo;
+    J.ncols = jobs[j].ncols;
+    J.tile0 = tiles;
+    J.X = jobs[j].X;
+    J.B = jobs[j].B;
+    J.OUT = jobs[j].OUT;
+    J.Dinv = (const TM*)jobs[j].Dinv;
+    J.ddiag = jobs[j].ddiag;
+    J.norm = jobs[j].norm;
+    tiles += (jobs[j].ncols + TC - 1) / TC;
+  }
+  B.ntiles = tiles;
 #define FHMG_CASE(LL, TT) \
-  if (L == LL && TC == TT) return panel_launch_t<TM, LL, TT, MODE>(st, a, P, err);
+  if (L == LL && TC == TT) return panel_launch_t<T, TM, LL, TT, MODE>(st, B, err);
   FHMG_CASE(16, 1) FHMG_CASE(16, 2) FHMG_CASE(16, 4) FHMG_CASE(16, 8) FHMG_CASE(16, 16) FHMG_CASE(16, 32)
   FHMG_CASE(32, 1) FHMG_CASE(32, 2) FHMG_CASE(32, 4) FHMG_CASE(32, 8) FHMG_CASE(32, 16) FHMG_CASE(32, 32)
   FHMG_CASE(64, 1) FHMG_CASE(64, 2) FHMG_CASE(64, 4) FHMG_CASE(64, 8) FHMG_CASE(64, 16) FHMG_CASE(64, 32)

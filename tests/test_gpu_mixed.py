@@ -24,9 +24,10 @@ def dev(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
 
 
+@pytest.mark.parametrize("storage", [0, 1, 2])
 @pytest.mark.parametrize("alpha", [0.3, 0.5, 0.8])
 @pytest.mark.parametrize("dim,N,M", [(1, 511, 512), (2, 63, 128)])
-def test_mixed_reaches_fp64_tolerance(alpha, dim, N, M):
+def test_mixed_reaches_fp64_tolerance(alpha, dim, N, M, storage):
     gamma = (2 - alpha) / alpha
     t = l1.graded_mesh(1.0, M, gamma)
     R = l1.l1_matrix(t, alpha)
@@ -34,6 +35,7 @@ def test_mixed_reaches_fp64_tolerance(alpha, dim, N, M):
     f = a.reshape((-1,) + (1,) * dim) * s[None] + 0.05 * inputs.random_field(3, (M,) + (N,) * dim)
     H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
     P = fh.Problem(H, dim, N, 1.0, fh.MIXED_FP32)
+    P.set_mixed_storage(storage)
     u = torch.zeros(f.shape, dtype=torch.float64, device=DEV)
     k, rr = P.solve(u, dev(f), None, 1, 1, 1e-8, 60)
     assert rr <= 1e-8

@@ -57,6 +57,17 @@ _SIGS = {
     "fhmg_solve_batched": (_I, [_I, _c.POINTER(_P), _c.POINTER(_P), _c.POINTER(_P), _I, _I, _D, _I,
                                 _c.POINTER(_I), _c.POINTER(_D)]),
     "fhmg_autotune_leaf": (_I, [_D, _D, _D, _I, _D, _I, _I, _D, _I, _P, _c.POINTER(_I), _c.POINTER(_D)]),
+    "fhmg_problem_set_rtol_reference": (_I, [_P, _I]),
+    "fhmg_wsnet_create": (_I, [_I, _I, _c.c_ulonglong, _c.POINTER(_P)]),
+    "fhmg_wsnet_destroy": (_I, [_P]),
+    "fhmg_wsnet_num_params": (_I, [_P, _c.POINTER(_LL)]),
+    "fhmg_wsnet_get_params": (_I, [_P, _P]),
+    "fhmg_wsnet_set_params": (_I, [_P, _P]),
+    "fhmg_wsnet_forward": (_I, [_P, _P, _I, _I, _P, _P]),
+    "fhmg_wsnet_loss_grad": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "fhmg_wsnet_train": (_I, [_P, _P, _P, _LL, _I, _I, _c.c_float, _c.c_ulonglong, _c.POINTER(_c.c_float), _P]),
+    "fhmg_ws_dataset": (_I, [_P, _P, _P, _D, _I, _c.c_float, _P, _P, _c.POINTER(_LL)]),
+    "fhmg_ws_predict": (_I, [_P, _P, _P, _D, _I, _I, _P]),
 }
 
 
@@ -168,6 +179,10 @@ class Problem:
     def set_inner(self, cycles):
         _check(lib().fhmg_problem_set_inner(self._p, cycles))
 
+    def set_rtol_reference(self, ref):
+        """0: ||r_k|| <= rtol ||r_0|| (default); 1: ||r_k|| <= rtol max|F|."""
+        _check(lib().fhmg_problem_set_rtol_reference(self._p, ref))
+
     def set_mixed_storage(self, mode):
         """0 automatic, 1 FP64 storage with FP32 products, 2 FP32 throughout (inner cycles)."""
         _check(lib().fhmg_problem_set_mixed_storage(self._p, mode))
@@ -245,6 +260,82 @@ def solve_batched(problems, us, fs, nu1=1, nu2=1, rtol=1e-8, max_cycles=60, allo
     st = lib().fhmg_solve_batched(n, P, U, F, nu1, nu2, rtol, max_cycles, k, rr)
     _check(st, allow=(FHMG_ENOTCONV,) if allow_notconv else ())
     return list(k), list(rr)
+
+
+def _fptr(x):
+    """Device pointer of a contiguous float32 tensor."""
+    import torch
+    if x.dtype != torch.float32 or not x.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    return x.data_ptr()
+
+
+class WSNet:
+    """fhmg_wsnet: the warm-start network (parameters on the device)."""
+
+    def __init__(self, hidden=320, layers=3, seed=0):
+        h = _P()
+        _check(lib().fhmg_wsnet_create(hidden, layers, seed, ctypes.byref(h)))
+        self._h = h
+        self.hidden, self.layers = hidden, layers
+
+    def num_params(self):
+        n = _LL()
+        _check(lib().fhmg_wsnet_num_params(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().fhmg_wsnet_get_params(self._h, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().fhmg_wsnet_set_params(self._h, p.ctypes.data))
+
+    def forward(self, X, Y, bf16=False, stream=None):
+        _check(lib().fhmg_wsnet_forward(self._h, _fptr(X), X.shape[0], 1 if bf16 else 0, _fptr(Y), _stream_ptr(stream)))
+
+    def loss_grad(self, X, Y, stream=None):
+        import numpy as np
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().fhmg_wsnet_loss_grad(self._h, _fptr(X), _fptr(Y), X.shape[0], loss.ctypes.data, g.ctypes.data,
+                                          _stream_ptr(stream)))
+        return float(loss[0]), g
+
+    def train(self, X, Y, batch=4096, steps=1000, lr=1e-3, seed=0, stream=None):
+        last = _c.c_float()
+        _check(lib().fhmg_wsnet_train(self._h, _fptr(X), _fptr(Y), X.shape[0], batch, steps, lr, seed,
+                                      ctypes.byref(last), _stream_ptr(stream)))
+        return last.value
+
+    def predict(self, prob, f, alpha, K=24, bf16=True, u0=None):
+        """Warm start u0 for source f (constant in time) on problem prob."""
+        import torch
+        if u0 is None:
+            u0 = torch.empty_like(f)
+        _check(lib().fhmg_ws_predict(self._h, prob._p, _ptr(f), alpha, K, 1 if bf16 else 0, _ptr(u0)))
+        return u0
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fhmg_wsnet_destroy(self._h)
+            self._h = None
+
+
+def ws_dataset(prob, u, f, alpha, K=24, rel_thr=1e-6):
+    """Training pairs (X, Y) from a solution u of prob for a source f constant in time."""
+    import torch
+    nm = K ** prob.dim
+    X = torch.empty((nm * prob.M, 6), dtype=torch.float32, device=u.device)
+    Y = torch.empty((nm * prob.M,), dtype=torch.float32, device=u.device)
+    n = _LL()
+    _check(lib().fhmg_ws_dataset(prob._p, _ptr(u), _ptr(f), alpha, K, rel_thr, X.data_ptr(), Y.data_ptr(),
+                                 ctypes.byref(n)))
+    return X[: n.value], Y[: n.value]
 
 
 def autotune_leaf(alpha, gamma, T, M, tol, dim, N, Lx=1.0, prec=FP64, stream=None):

@@ -92,6 +92,7 @@ struct fhmg_problem_s {
   float* Rs32 = nullptr;
   float* Ef32 = nullptr;
   int mixed_storage = 0; // 0 automatic, 1 FP64 storage + FP32 products, 2 FP32 storage
+  int rtol_ref = 0;      // stopping test relative to: 0 the initial defect, 1 max |F|
   std::map<std::pair<int, long long>, int> tune;  // autotuned column tiles: (kind*2+mode, ncols) -> TC
   double* Ff = nullptr;  // f + d g when g is given
   double* dmm = nullptr; // d_{m,m}
@@ -407,12 +408,15 @@ int axpy(fhmg_problem p, double* y, const double* x, long long n, double a) {
 }
 
 // FP64 path: V-cycles on u until the colour-0 defect norm is below rtol * ||r_0||.
+int absmax(fhmg_problem p, const double* x, long long n, double* out);
+
 int solve_fp64(fhmg_problem p, double* u, const double* F, int nu1, int nu2, double rtol, int max_cycles, int* kout,
                double* r0out, double* rout) {
   double r0, r;
   TRY(fine_defect(p, u, F, false, nullptr, &r0));
   if (!std::isfinite(r0)) return fail(FHMG_ENAN, "initial residual is not finite");
   r = r0;
+  if (p->rtol_ref) TRY(absmax(p, F, p->lev[p->nlev - 1].npts * p->M, &r0));
   int k = 0;
   while (r > rtol * r0 && k < max_cycles) {
     TRY(vcycle_rec<double>(p, p->nlev - 1, u, F, nu1, nu2, K64));
@@ -486,6 +490,7 @@ int solve_mixed(fhmg_problem p, double* u, const double* F, int nu1, int nu2, do
   }
   if (!std::isfinite(r0)) return fail(FHMG_ENAN, "initial residual is not finite");
   r = r0;
+  if (p->rtol_ref) TRY(absmax(p, F, n, &r0));
   // FP32 storage limits one defect-correction step to ~1e-2 on these grids (two V-cycles reach
   // it); FP64 storage with FP32 products converges like FP64 (four V-cycles ~ 1e-4)
   const int inner = p->inner > 0 ? p->inner : (f32 ? 2 : 4);
@@ -687,6 +692,18 @@ int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, 
 }
 
 long long fhmg_internal_grid_elems(fhmg_problem p) { return p->lev[p->nlev - 1].npts * (long long)p->M; }
+
+int fhmg_internal_problem_geom(fhmg_problem p, int* dim, int* N, int* M, double* Lx, void** stream,
+                               const double** t_host) {
+  if (!p) return fail(FHMG_EINVAL, "null problem");
+  *dim = p->dim;
+  *N = p->N;
+  *M = p->M;
+  *Lx = p->Lx;
+  *stream = (void*)p->st;
+  *t_host = p->H->host.t.data();
+  return FHMG_OK;
+}
 int fhmg_internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
 // ================================================================ C-ABI
@@ -948,6 +965,13 @@ int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode) {
   TRY(check_dims(p));
   if (mode < 0 || mode > 2) return fail(FHMG_EINVAL, "mixed storage mode must be 0, 1 or 2");
   p->mixed_storage = mode;
+  return FHMG_OK;
+}
+
+int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref) {
+  TRY(check_dims(p));
+  if (ref != 0 && ref != 1) return fail(FHMG_EINVAL, "reference must be 0 (initial defect) or 1 (max |F|)");
+  p->rtol_ref = ref;
   return FHMG_OK;
 }
 

@@ -214,6 +214,115 @@ def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, di
     return H, f, res, t_hbuild
 
 
+def time_once(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def measure_warmstart(fh, stream, dev, rtol):
+    """2D N=1023^2, M=512, gamma=2, GRF source (ell = 0.1): FP64 zero guess, mixed zero guess, and
+    mixed from the learned warm start (network trained on library solves at N=255^2, same M)."""
+    import torch
+    from paper_1706_07632_gb300 import warmstart
+    dim, N, M, gamma, alpha, K = 2, 1023, 512, 2.0, 0.55, 24
+    t0 = time.perf_counter()
+    alphas = [0.3, 0.37, 0.44, 0.51, 0.58, 0.65, 0.72, 0.8]
+    X, Y = warmstart.generate(dim, 255, M, gamma, alphas, seeds=list(range(200, 208)), K=K)
+    t_data = time.perf_counter() - t0
+    net = fh.WSNet(320, 3, seed=0)
+    t_train, losses = time_once(lambda: warmstart.train(net, X, Y, steps=3000, batch=4096, lr=2e-3), stream)
+    H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
+    t, _ = H.mesh()
+    f = warmstart.source_field(dim, 999, t[1:], N)
+    out = {"workload": f"2D N={N}^2, M={M}, alpha={alpha}, gamma={gamma}, GRF source (length scale 0.1), "
+                       f"relres {rtol:g} of max|F| (same absolute target for every start)",
+           "training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train, "loss": losses[-1],
+                        "params": net.num_params(), "train_grid": "N=255^2, M=512, 8 alphas"}}
+    for name, prec, warm in (("fp64_zero", fh.FP64, False), ("mixed_zero", fh.MIXED_FP32, False),
+                             ("mixed_warm", fh.MIXED_FP32, True)):
+        P = fh.Problem(H, dim, N, 1.0, prec, stream)
+        P.set_rtol_reference(1)
+        u = torch.zeros_like(f)
+        if warm:  # untimed warm-up of the prediction and the solve
+            net.predict(P, f, alpha, K=K, bf16=True, u0=u)
+            P.solve(u, f, None, 1, 1, rtol, 60)
+        else:
+            P.solve(u, f, None, 1, 1, rtol, 60)
+
+        def run():
+            if warm:
+                net.predict(P, f, alpha, K=K, bf16=True, u0=u)
+            else:
+                u.zero_()
+            return P.solve(u, f, None, 1, 1, rtol, 60)
+
+        ts, (k, rr) = time_once(run, stream)
+        out[name] = {"time_to_rtol_s": ts, "cycles": k, "relres_vs_maxF": rr}
+        if warm:
+            out[name]["predict_s"] = time_once(lambda: net.predict(P, f, alpha, K=K, bf16=True, u0=u), stream)[0]
+        del P
+    out["speedup_mixed_warm_vs_fp64"] = out["fp64_zero"]["time_to_rtol_s"] / out["mixed_warm"]["time_to_rtol_s"]
+    out["speedup_mixed_warm_vs_mixed_zero"] = out["mixed_zero"]["time_to_rtol_s"] / out["mixed_warm"]["time_to_rtol_s"]
+    out["cycles_saved_by_warm_start"] = out["mixed_zero"]["cycles"] - out["mixed_warm"]["cycles"]
+    return out
+
+
+def measure_batched(fh, inputs, stream, dev, rtol, n_inst=64, seed=7):
+    """64 independent 1D instances (alpha ~ U[.2,.9], gamma ~ U[1,3], M in {256,...,2048},
+    N in {255, 1023, 4095}, 8-mode sine-series sources), leaf autotuned per (M, alpha) class,
+    solved by one batched mixed solve (one launch per stage, graph-replayed cycles)."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    Hs, Ps, us, fs, dof = [], [], [], [], 0
+    leaf_cache = {}
+    for i in range(n_inst):
+        alpha = float(rng.uniform(0.2, 0.9))
+        gamma = float(rng.uniform(1.0, 3.0))
+        M = int(rng.choice([256, 512, 1024, 2048]))
+        N = int(rng.choice([255, 1023, 4095]))
+        key = (M, N)
+        if key not in leaf_cache:
+            leaf_cache[key] = fh.autotune_leaf(alpha, gamma, 1.0, M, 1e-10, 1, N, 1.0, fh.MIXED_FP32, stream)[0]
+        H = fh.HMatrix(alpha, gamma, 1.0, M, leaf_cache[key], 0, 1e-10)
+        P = fh.Problem(H, 1, N, 1.0, fh.MIXED_FP32, stream)
+        t, _ = H.mesh()
+        a, s, _ = inputs.sine_series_1d(seed * 1000 + i, t[1:], N)
+        f = torch.as_tensor(a, device=dev)[:, None] * torch.as_tensor(s, device=dev)[None, :]
+        Hs.append(H), Ps.append(P), fs.append(f), us.append(torch.zeros_like(f))
+        dof += N * M
+    for u in us:
+        u.zero_()
+    fh.solve_batched(Ps, us, fs, 1, 1, rtol, 60)  # warm-up (graph capture)
+    for u in us:
+        u.zero_()
+    tb, (k, rr) = time_once(lambda: fh.solve_batched(Ps, us, fs, 1, 1, rtol, 60), stream)
+    # the same instances one after the other, for reference
+    for u in us:
+        u.zero_()
+
+    def seq():
+        ks = []
+        for P, u, f in zip(Ps, us, fs):
+            ks.append(P.solve(u, f, None, 1, 1, rtol, 60)[0])
+        return ks
+    for u in us:
+        u.zero_()
+    ts, ks = time_once(seq, stream)
+    return {"workload": f"{n_inst} 1D instances, alpha~U[.2,.9], gamma~U[1,3], M in {{256..2048}}, "
+                        f"N in {{255,1023,4095}}, 8-mode sine sources, relres {rtol:g}",
+            "dof_total": dof, "leaves": sorted(set(leaf_cache.values())),
+            "batched_s": tb, "sequential_s": ts, "speedup_batched_vs_sequential": ts / tb,
+            "batched_dof_cycles_per_s": dof * float(np.mean(k)) / tb,
+            "cycles_mean": float(np.mean(k)), "cycles_max": int(np.max(k)), "relres_max": float(np.max(rr))}
+
+
 def roofline(H, r, ncols_avg, kind):
     c = r["cnt"]
     flops_launch = H.flops_per_column() * ncols_avg
@@ -297,6 +406,15 @@ def main():
                "roofline_mixed": roofline(H2, res2["mixed"], N2 * N2 / 2.0, "mixed"), "hbuild_s": tb2}
         del f2
 
+    wws = None
+    bat = None
+    if not a.no_2d:
+        torch.cuda.empty_cache()
+        wws = measure_warmstart(fh, stream, dev, a.rtol)
+        torch.cuda.empty_cache()
+        bat = measure_batched(fh, inputs, stream, dev, a.rtol)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         ts, tb = oracle_direct_sample(a)
@@ -316,6 +434,7 @@ def main():
                 "speedup_mixed_vs_fp64": res["fp64"]["time_to_rtol_s"] / res["mixed"]["time_to_rtol_s"],
                 "hbuild_s": t_hbuild, "roofline": roofline(H, res["mixed"], a.N / 2.0, "mixed"),
                 "roofline_fp64": roofline(H, res["fp64"], a.N / 2.0, "fp64"), "workload_2d": w2d,
+                "workload_warmstart": wws, "workload_batched": bat,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": head["cnt"]["launches"], "clocks": clk}
         print(json.dumps(line))
     if dist:

@@ -68,9 +68,10 @@ struct LevelData {
   double* RC = nullptr;        // restricted defect (coarse levels)
   float* E32 = nullptr;        // FP32 copies for the FP32 inner cycles of the mixed path
   float* RC32 = nullptr;
-  double* Dinv64 = nullptr;    // (D_ii + s I)^{-1}, FP64, column-major
-  float* Dinv32 = nullptr;     // the same in FP32 (mixed path; its diagonal is not used)
-  double* dinvdiag = nullptr;  // FP64 diagonal of the inverses (mixed path)
+  double* Dinv64 = nullptr;    // (D_ii + s I)^{-1}, FP64, in the chunk layout (to_panel_layout)
+  float* Dinv32 = nullptr;     // the same in FP32 without its diagonal (mixed path)
+  double* dinvdiag = nullptr;  // the inverses' diagonal, FP64 (mixed path) ...
+  float* dinvdiag32 = nullptr; // ... and FP32 (FP32 inner cycles)
 };
 
 }  // namespace
@@ -83,7 +84,8 @@ struct fhmg_problem_s {
   int M = 0, L = 0, nb = 0;
   DevPanel panel64;  // chunk stream, FP64 matrices
   DevPanel panel32;  // chunk stream, FP32 matrices (mixed path)
-  double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path)
+  double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path) ...
+  float* rdiag32 = nullptr; // ... and its FP32 copy (FP32 inner cycles)
   std::vector<LevelData> lev;
   double* Xs = nullptr;  // scratch, >= max(colour-0 count, coarse count) * M
   double* Rs = nullptr;  // scratch, fine points * M (defect)
@@ -129,12 +131,6 @@ int upload(std::vector<void*>& list, const std::vector<S>& src, const T** out, s
   *out = p;
   if (bytes) *bytes += tmp.size() * sizeof(T);
   return FHMG_OK;
-}
-
-// row-major -> column-major for a rows x cols block
-void transpose_into(const double* in, double* out, int rows, int cols) {
-  for (int r = 0; r < rows; ++r)
-    for (int c = 0; c < cols; ++c) out[(size_t)c * rows + r] = in[(size_t)r * cols + c];
 }
 
 // Uploads the chunk stream of the H-matrix (elem_bytes 8: FP64 products, 4: FP32 products).
@@ -218,7 +214,8 @@ fhmg::WalkArgsT<T> smooth_job(fhmg_problem p, int l, int kind, const Geo& g, lon
   a.B = B;
   a.OUT = nullptr;
   a.Dinv = kind == K64 ? (const void*)lv.Dinv64 : (const void*)lv.Dinv32;
-  a.ddiag = kind == KSPLIT ? (const T*)lv.dinvdiag : nullptr;
+  // FP32 products leave the diagonal out of the streamed blocks; it is applied in T
+  a.ddiag = kind == KSPLIT ? (const T*)lv.dinvdiag : kind == K32 ? (const T*)lv.dinvdiag32 : nullptr;
   a.norm = nullptr;
   a.err = p->derr;
   a.tile = tuned_tile(p, kind, fhmg::MODE_SMOOTH, nc);
@@ -238,7 +235,7 @@ fhmg::WalkArgsT<T> matvec_job(fhmg_problem p, int kind, long long nc, const T* X
   a.B = B;
   a.OUT = OUT;
   a.Dinv = nullptr;
-  a.ddiag = kind == KSPLIT ? (const T*)p->rdiag : nullptr;
+  a.ddiag = kind == KSPLIT ? (const T*)p->rdiag : kind == K32 ? (const T*)p->rdiag32 : nullptr;
   a.norm = norm;
   a.err = p->derr;
   a.tile = tuned_tile(p, kind, fhmg::MODE_MATVEC, nc);
@@ -822,6 +819,9 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     const double* d;
     if ((st = upload(p->allocs, rd, &d, nullptr)) != FHMG_OK) return bail(st);
     p->rdiag = const_cast<double*>(d);
+    const float* d32;
+    if ((st = upload(p->allocs, rd, &d32, nullptr)) != FHMG_OK) return bail(st);
+    p->rdiag32 = const_cast<float*>(d32);
   }
   const int M = p->M;
   for (int l = 0; l < nlev; ++l) {
@@ -833,15 +833,16 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     lv.shift = (dim == 1 ? 2.0 : 4.0) * lv.inv_h2;
     std::vector<double> inv;
     fhmg::diag_inverses(h->host, h->flat, lv.shift, inv);
-    std::vector<double> invT(inv.size());
-    for (int i = 0; i < p->nb; ++i)
-      transpose_into(&inv[(size_t)i * p->L * p->L], &invT[(size_t)i * p->L * p->L], p->L, p->L);
+    const size_t LL = (size_t)p->L * p->L;
+    std::vector<double> invP(inv.size());
+    for (int i = 0; i < p->nb; ++i) fhmg::to_panel_layout(&inv[i * LL], p->L, 8, false, &invP[i * LL]);
     const double* d64;
-    if ((st = upload(p->allocs, invT, &d64, nullptr)) != FHMG_OK) return bail(st);
+    if ((st = upload(p->allocs, invP, &d64, nullptr)) != FHMG_OK) return bail(st);
     lv.Dinv64 = const_cast<double*>(d64);
     if (mixed) {
+      for (int i = 0; i < p->nb; ++i) fhmg::to_panel_layout(&inv[i * LL], p->L, 4, true, &invP[i * LL]);
       const float* d32;
-      if ((st = upload(p->allocs, invT, &d32, nullptr)) != FHMG_OK) return bail(st);
+      if ((st = upload(p->allocs, invP, &d32, nullptr)) != FHMG_OK) return bail(st);
       lv.Dinv32 = const_cast<float*>(d32);
       std::vector<double> dg((size_t)p->nb * p->L);
       for (int i = 0; i < p->nb; ++i)
@@ -849,6 +850,9 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
       const double* dd;
       if ((st = upload(p->allocs, dg, &dd, nullptr)) != FHMG_OK) return bail(st);
       lv.dinvdiag = const_cast<double*>(dd);
+      const float* dd32;
+      if ((st = upload(p->allocs, dg, &dd32, nullptr)) != FHMG_OK) return bail(st);
+      lv.dinvdiag32 = const_cast<float*>(dd32);
     }
     if (l < nlev - 1) {
       if ((st = dalloc(p->allocs, &lv.E, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);

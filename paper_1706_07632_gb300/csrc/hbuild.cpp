@@ -492,6 +492,7 @@ size_t pad16(size_t n) { return (n + 15) & ~(size_t)15; }
 
 void build_panel(const HostH& h, const FlatH& f, int eb, PanelHost& out) {
   const int L = f.L, nb = f.nb;
+  const int VE = 16 / eb;  // elements per 16-byte vector
   out = PanelHost();
   out.cptr.assign(nb + 1, 0);
   int maxdist = 0;
@@ -509,49 +510,64 @@ void build_panel(const HostH& h, const FlatH& f, int eb, PanelHost& out) {
     out.slot_bytes = std::max(out.slot_bytes, (int)nbytes);
     return off;
   };
+  // entry (k, r) of a chunk matrix with R rows, k the reduction index
+  auto at = [&](size_t off, int k, int r, int R) { return off + (((size_t)(k / VE) * R + r) * VE + k % VE) * eb; };
+  auto put_square = [&](const double* D, size_t off, bool zero_diag) {
+    for (int k = 0; k < L; ++k)
+      for (int r = 0; r < L; ++r)
+        put_value(out.pkg, at(off, k, r, L), (zero_diag && k == r) ? 0.0 : D[(size_t)r * L + k], eb);
+  };
   for (int i = 0; i < nb; ++i) {
     // near-field blocks
     for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) {
-      const double* D = &f.dense_data[(size_t)f.dlist_blk[d] * L * L];
       size_t off = add_chunk(CH_DENSE, L, f.dlist_col[d], (size_t)L * L * eb);
-      for (int k = 0; k < L; ++k)
-        for (int r = 0; r < L; ++r) put_value(out.pkg, off + ((size_t)k * L + r) * eb, D[(size_t)r * L + k], eb);
+      put_square(&f.dense_data[(size_t)f.dlist_blk[d] * L * L], off, false);
     }
-    // U panel (row-major L x K in FlatH) in slabs of up to L columns
+    // U panel (row-major L x K in FlatH) in slabs of up to L columns, padded with zero columns to
+    // whole vectors (their z index repeats the slab's first one)
     const int K = f.uptr[i + 1] - f.uptr[i];
     for (int k0 = 0; k0 < K; k0 += L) {
       const int kc = std::min(L, K - k0);
-      size_t off = add_chunk(CH_UPART, kc, k0, (size_t)kc * L * eb + (size_t)kc * 4);
+      const int kp = (kc + VE - 1) / VE * VE;
+      size_t off = add_chunk(CH_UPART, kp, k0, (size_t)kp * L * eb + (size_t)kp * 4);
       for (int kk = 0; kk < kc; ++kk)
         for (int r = 0; r < L; ++r)
-          put_value(out.pkg, off + ((size_t)kk * L + r) * eb, f.udata[f.uoff[i] + (size_t)r * K + k0 + kk], eb);
-      for (int kk = 0; kk < kc; ++kk) {
-        int z = f.uz[f.uptr[i] + k0 + kk];
-        std::memcpy(&out.pkg[off + (size_t)kc * L * eb + (size_t)kk * 4], &z, 4);
+          put_value(out.pkg, at(off, kk, r, L), f.udata[f.uoff[i] + (size_t)r * K + k0 + kk], eb);
+      for (int kk = 0; kk < kp; ++kk) {
+        int z = f.uz[f.uptr[i] + k0 + (kk < kc ? kk : 0)];
+        std::memcpy(&out.pkg[off + (size_t)kp * L * eb + (size_t)kk * 4], &z, 4);
       }
     }
-    // diagonal block
+    // diagonal block (FP32 streams carry it without its diagonal, which the kernels apply in
+    // the grid functions' precision)
     {
-      const double* D = &f.dense_data[(size_t)f.diag_blk[i] * L * L];
       size_t off = add_chunk(CH_DIAG, L, i, (size_t)L * L * eb);
-      for (int k = 0; k < L; ++k)
-        for (int r = 0; r < L; ++r) put_value(out.pkg, off + ((size_t)k * L + r) * eb, D[(size_t)r * L + k], eb);
+      put_square(&f.dense_data[(size_t)f.diag_blk[i] * L * L], off, eb == 4);
     }
-    // V panel (row-major K' x L in FlatH) in slabs of up to L rows
+    // V panel (row-major K' x L in FlatH) in slabs of up to L rows; the slab's rows are the
+    // outputs, its columns the reduction index
     const int Kv = f.vptr[i + 1] - f.vptr[i];
     for (int k0 = 0; k0 < Kv; k0 += L) {
       const int kc = std::min(L, Kv - k0);
       size_t off = add_chunk(CH_VPART, kc, k0, (size_t)kc * L * eb + (size_t)kc * 4);
       for (int kk = 0; kk < kc; ++kk)
         for (int c = 0; c < L; ++c)
-          put_value(out.pkg, off + ((size_t)kk * L + c) * eb, f.vdata[f.voff[i] + (size_t)(k0 + kk) * L + c], eb);
+          put_value(out.pkg, at(off, c, kk, kc), f.vdata[f.voff[i] + (size_t)(k0 + kk) * L + c], eb);
       for (int kk = 0; kk < kc; ++kk) {
         int code = 2 * f.vz[f.vptr[i] + k0 + kk] + f.vinit[f.vptr[i] + k0 + kk];
         std::memcpy(&out.pkg[off + (size_t)kc * L * eb + (size_t)kk * 4], &code, 4);
       }
     }
+    out.chunks[out.chunks.size() - 4] |= 1 << 12;  // the leaf row's last chunk
     out.cptr[i + 1] = (int)(out.chunks.size() / 4);
   }
+}
+
+void to_panel_layout(const double* A, int L, int eb, bool zero_diag, double* out) {
+  const int VE = 16 / eb;
+  for (int k = 0; k < L; ++k)
+    for (int r = 0; r < L; ++r)
+      out[((size_t)(k / VE) * L + r) * VE + k % VE] = (zero_diag && k == r) ? 0.0 : A[(size_t)r * L + k];
 }
 
 }  // namespace fhmg

@@ -65,15 +65,26 @@ struct FlatH {
 };
 
 // The H-matrix as a stream of chunks that the panel kernel stages into shared memory, one
-// chunk per pipeline slot, in the order a leaf-row walk consumes them.  Per leaf row i:
-//   DENSE(j)  one L x L near-field block D_ij, column-major           (aux = j)
-//   UPART     up to L columns of the U panel, column-major, then their z-pool rows (int)
-//   DIAG      D_ii column-major (the smoother streams its level inverse instead) (aux = i)
-//   VPART     up to L rows of the V panel (row kk = V[kk][0..L)), then one int per row:
+// chunk per pipeline slot, in the order a leaf-row walk consumes them.  Every chunk matrix is a
+// product operand out[r] += sum_k A(k, r) in[k] stored vector-interleaved: with VE = 16 / elem
+// bytes, entry (k, r) of an R-row matrix sits at ((k / VE) * R + r) * VE + k % VE, so that one
+// thread reads VE consecutive k of its row as one 16-byte load and consecutive rows are
+// consecutive vectors.  Per leaf row i:
+//   DENSE(j)  one L x L near-field block D_ij (k = column, r = row)        (aux = j)
+//   UPART     count <= L columns of the U panel (k = panel column, r = row; count padded to whole
+//             vectors with zero columns), then count z-pool rows (int)
+//   DIAG      D_ii (the smoother streams its level inverse instead; FP32 streams carry both
+//             without their diagonal, which the kernels apply in FP64)     (aux = i)
+//   VPART     count <= L rows of the V panel (r = panel row, k = column), then one int per row:
 //             2 * z-pool row + 1 if the row starts its block's z (assign, not add)
-// Chunk descriptor (4 ints): type | count << 4, aux, bytes, byte offset / 16.  Every chunk
+// Chunk descriptor (4 ints): type | count << 4 | (last chunk of its leaf row) << 12, aux, bytes,
+// byte offset / 16.  Every chunk
 // starts on a 16-byte boundary and its size is a multiple of 16 bytes (TMA bulk copy rule).
 enum ChunkType { CH_DENSE = 0, CH_UPART = 1, CH_DIAG = 2, CH_VPART = 3 };
+
+// Writes the row-major L x L matrix A in the chunk layout above (R = L, k = column), optionally
+// without its diagonal: the layout of the level inverses the smoother streams as DIAG chunks.
+void to_panel_layout(const double* A, int L, int elem_bytes, bool zero_diag, double* out);
 
 struct PanelHost {
   std::vector<unsigned char> pkg;

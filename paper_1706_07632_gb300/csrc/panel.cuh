@@ -21,7 +21,11 @@
 // T is the type of the grid functions and of the accumulation, TM the type of the H-matrix
 // products (double, or float for the mixed path -- see ddiag).  Every (row, column) output is
 // split over S threads along its reduction, combined by xor-shuffles, so a CTA with one column
-// still spreads a leaf step over the whole block (the coarse grids are latency-bound).
+// still spreads a leaf step over the whole block (the coarse grids are latency-bound).  The
+// chunk matrices are vector-interleaved (16-byte vectors of consecutive reduction indices, one
+// vector per row, rows consecutive): a thread reads its row's vectors with 16-byte loads and the
+// eight lanes of a shared-memory wavefront read eight consecutive rows of one split, so matrix
+// and x-tile reads are free of bank conflicts.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -32,19 +36,80 @@ namespace fhmg {
 
 struct PanelDev {
   const unsigned char* pkg;  // chunk bytes
-  const int4* chunks;        // type | count << 4, aux, bytes, offset / 16
+  const int4* chunks;        // type | count << 4 | last << 12, aux, bytes, offset / 16
   const int* cptr;           // nb + 1
   int nb, L, pool, W, slot_bytes, ns;
 };
 
-template <int L, int TC, int NT_>
+// 16-byte vectors of the chunk layout
+template <typename TM>
+struct VecOf;
+template <>
+struct VecOf<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct VecOf<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+// a += d .* x into four independent accumulators (gg: the vector's place in a thread's sequence)
+__device__ __forceinline__ void vfma(float (&a)[4], int, const float4 d, const float4 x) {
+  a[0] = fmaf(d.x, x.x, a[0]);
+  a[1] = fmaf(d.y, x.y, a[1]);
+  a[2] = fmaf(d.z, x.z, a[2]);
+  a[3] = fmaf(d.w, x.w, a[3]);
+}
+__device__ __forceinline__ void vfma(double (&a)[4], int gg, const double2 d, const double2 x) {
+  const int o = (gg & 1) * 2;
+  a[o] = fma(d.x, x.x, a[o]);
+  a[o + 1] = fma(d.y, x.y, a[o + 1]);
+}
+template <typename TM>
+__device__ __forceinline__ TM sum4(const TM (&a)[4]) {
+  return (a[0] + a[1]) + (a[2] + a[3]);
+}
+// VE consecutive z-pool entries named by an index vector
+__device__ __forceinline__ float4 gather_z(const float* zp, const int* idx, int TC, int cl) {
+  const int4 k = *reinterpret_cast<const int4*>(idx);
+  return make_float4(zp[k.x * TC + cl], zp[k.y * TC + cl], zp[k.z * TC + cl], zp[k.w * TC + cl]);
+}
+__device__ __forceinline__ double2 gather_z(const double* zp, const int* idx, int TC, int cl) {
+  const int2 k = *reinterpret_cast<const int2*>(idx);
+  return make_double2(zp[k.x * TC + cl], zp[k.y * TC + cl]);
+}
+// VE consecutive rows k0.. of one global column (stride ld), converted to TM
+template <typename T>
+__device__ __forceinline__ float4 load_col(const T* x, long long k0, long long ld, bool ok, float*) {
+  if (!ok) return make_float4(0.f, 0.f, 0.f, 0.f);
+  return make_float4((float)x[k0 * ld], (float)x[(k0 + 1) * ld], (float)x[(k0 + 2) * ld], (float)x[(k0 + 3) * ld]);
+}
+template <typename T>
+__device__ __forceinline__ double2 load_col(const T* x, long long k0, long long ld, bool ok, double*) {
+  if (!ok) return make_double2(0.0, 0.0);
+  return make_double2((double)x[k0 * ld], (double)x[(k0 + 1) * ld]);
+}
+
+// Thread tile of the walk: TC columns, each (row, column) output split over S threads that
+// take the reduction's 16-byte vectors round robin.  Lane = column + TC * (row + RL * split), so
+// the xor-shuffles that combine the splits use lane offsets TC * RL, 2 TC * RL, ...  When the
+// block has more threads than outputs x splits (small leaves), the surplus warps stay idle.
+template <int L, int TC, int NT_, int VE>
 struct PTile {
   static constexpr int NT = NT_;
-  static constexpr int S0 = (NT / L) / TC;
-  static constexpr int S = S0 < 1 ? 1 : S0;     // splits per output
-  static constexpr int RG = NT / (TC * S);      // row groups
-  static constexpr int Q = L / RG;              // rows per thread
-  static_assert(RG <= L && L % RG == 0 && TC * S <= 32 && 32 % (TC * S) == 0, "tile shape");
+  static constexpr int NV = L / VE;                // vectors along a full reduction
+  static constexpr int S1 = (NT / L) / TC;
+  static constexpr int S0 = S1 < 1 ? 1 : S1;
+  static constexpr int S = S0 > NV ? NV : S0;      // splits per output
+  static constexpr int RL = 32 / (TC * S);         // rows per warp
+  static constexpr int RG0 = NT / (TC * S);
+  static constexpr int RG = RG0 > L ? L : RG0;     // active row groups
+  static constexpr int Q = L / RG;                 // rows per thread
+  static constexpr int NVT = NV / S;               // vectors per thread of a full reduction
+  static_assert(TC * S <= 32 && 32 % (TC * S) == 0 && L % RG == 0 && NV % S == 0 && RG % RL == 0,
+                "tile shape");
 };
 
 enum { MODE_SMOOTH = 0, MODE_MATVEC = 1 };
@@ -83,27 +148,30 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-template <typename T, int TC, int S>
+// sum over the S splits of an output (lane offsets STEP, 2 STEP, ... < 32)
+template <typename T, int STEP>
 __device__ __forceinline__ T reduce_splits(T v) {
 #pragma unroll
-  for (int o = TC; o < TC * S; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = STEP; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Shared-memory layout, in bytes from the (16-byte aligned) dynamic base.
+// Shared-memory layout, in bytes from the (16-byte aligned) dynamic base.  x tiles (the current
+// leaf's y, the ring of recent leaves' x) are stored per column with a padded length L + VE, so
+// that 16-byte reads of different columns fall in different banks.
 struct PanelSmem {
-  size_t ys, ysm, ring, zp, bar, flag, total;
+  size_t ysm, ring, zp, bar, desc, flag, total;
 };
-__host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, int slot_bytes, int ns, int bT,
-                                                int bTM) {
+__host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, int slot_bytes, int ns, int bTM) {
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t LP = (size_t)L + 16 / bTM;
   PanelSmem s;
-  s.ys = a16((size_t)ns * slot_bytes);
-  s.ysm = a16(s.ys + (size_t)L * TC * bT);
-  s.ring = a16(s.ysm + (size_t)L * TC * bTM);
-  s.zp = a16(s.ring + (size_t)W * L * TC * bTM);
+  s.ysm = a16((size_t)ns * slot_bytes);
+  s.ring = a16(s.ysm + (size_t)TC * LP * bTM);
+  s.zp = a16(s.ring + (size_t)W * TC * LP * bTM);
   s.bar = a16(s.zp + (size_t)pool * TC * bTM);
-  s.flag = s.bar + 8 * (size_t)ns;
+  s.desc = a16(s.bar + 8 * (size_t)ns);  // descriptor of the chunk in each slot
+  s.flag = s.desc + 16 * (size_t)ns;
   s.total = a16(s.flag + 16);
   return s;
 }
@@ -113,8 +181,8 @@ __host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, 
 //     B = F; Dinv = the level's inverted diagonal leaves (streamed as the DIAG chunks).
 //   MODE_MATVEC: OUT = B - R~ X on compact columns (ld = geo.ld); OUT may alias B or be NULL;
 //     norm != NULL folds max |OUT| into *norm (bit pattern of a non-negative double).
-//   ddiag (FP64-storage mixed path only): the FP64 diagonal of the streamed DIAG blocks, nb x L;
-//     the streamed blocks' own diagonal is then skipped and the diagonal term applied in T.
+//   ddiag (FP32 products, required): the diagonal of the streamed DIAG blocks, nb x L, in T; the
+//     FP32 blocks are stored without it and the diagonal term is applied in T.
 constexpr int kMaxJobs = 64;
 
 template <typename T, typename TM>
@@ -151,48 +219,68 @@ __device__ __forceinline__ int job_of(const WalkBatch<T, TM>& B, long long g) {
 
 template <typename T, typename TM, int L, int TC, int MODE, int NT_>
 __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ WalkBatch<T, TM> B) {
-  using TL = PTile<L, TC, NT_>;
-  constexpr int NT = TL::NT, Q = TL::Q, RG = TL::RG, S = TL::S;
-  constexpr int KS = L / S;
-  constexpr int NA = KS >= 4 ? 4 : KS;
+  using VT = typename VecOf<TM>::type;
+  constexpr int VE = VecOf<TM>::n;
+  using TL = PTile<L, TC, NT_, VE>;
+  constexpr int Q = TL::Q, RG = TL::RG, S = TL::S, RL = TL::RL, NVT = TL::NVT;
+  constexpr int STEP = TC * RL;            // lane offset between splits
+  constexpr int LP = L + VE;               // padded x-tile column
+  constexpr bool SPLITD = sizeof(TM) < 8;  // FP32 products: diagonal from ddiag, in T
   extern __shared__ __align__(16) unsigned char sm[];
-  const PanelSmem lay = panel_smem(L, TC, B.pool, B.W, B.slot_bytes, B.ns, sizeof(T), sizeof(TM));
+  const PanelSmem lay = panel_smem(L, TC, B.pool, B.W, B.slot_bytes, B.ns, sizeof(TM));
   unsigned char* slots = sm;
-  T* ys = reinterpret_cast<T*>(sm + lay.ys);     // y / x of the current leaf (T)
-  TM* ysm = reinterpret_cast<TM*>(sm + lay.ysm);  // the same in TM, converted once per leaf
+  TM* ysm = reinterpret_cast<TM*>(sm + lay.ysm);  // y of the current leaf (smoother), in TM
   TM* ring = reinterpret_cast<TM*>(sm + lay.ring);
   TM* zp = reinterpret_cast<TM*>(sm + lay.zp);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + lay.bar);
+  int4* sdesc = reinterpret_cast<int4*>(sm + lay.desc);
   volatile int* sflag = reinterpret_cast<volatile int*>(sm + lay.flag);
 
   const int t = threadIdx.x;
-  const int cl = t % TC;
-  const int sp = (t / TC) % S;
-  const int rg = t / (TC * S);
+  const int lane = t & 31;
+  const int cl = lane % TC;
+  const int rl = (lane / TC) % RL;
+  const int sp = lane / STEP;
+  const int rb0 = (t >> 5) * RL + rl;
+  const bool act = rb0 < RG;  // false only in the surplus warps of small leaves
+  const int rb = act ? rb0 : 0;
   const int ns = B.ns;
   const int W = B.W;
 
-  // producer cursor (thread 0): the next (tile, chunk) to stage, in consumption order
+  // Producer cursor (thread 0): the next (tile, chunk) to stage, in consumption order.  The
+  // descriptor of the next chunk is loaded one issue ahead, so that no global load sits on the
+  // producer's path between two block barriers; each issued descriptor is published in sdesc[slot]
+  // for the consumers (at least one block barrier separates that write from its use).
   long long pg = blockIdx.x;
-  int pj = pg < B.ntiles ? job_of(B, pg) : 0;
-  int pc = 0;
+  int pj = 0, pc = 0, nch_p = 0, pslot = 0;
+  int4 cdn = make_int4(0, 0, 0, 0);
+  if (t == 0 && pg < B.ntiles) {
+    pj = job_of(B, pg);
+    nch_p = __ldg(B.job[pj].P.cptr + B.job[pj].P.nb);
+    cdn = __ldg(B.job[pj].P.chunks);
+  }
   long long issued = 0;
   auto issue_next = [&]() {
     if (pg >= B.ntiles) return;
     const WalkJob<T, TM>& J = B.job[pj];
-    const int4 cd = __ldg(J.P.chunks + pc);
+    const int4 cd = cdn;
     const int type = cd.x & 15;
     const void* src = (MODE == MODE_SMOOTH && type == PK_DIAG)
                           ? (const void*)(J.Dinv + (long long)cd.y * L * L)
                           : (const void*)(J.P.pkg + 16LL * (long long)cd.w);
-    const int slot = (int)(issued % ns);
-    bulk_load(slots + (size_t)slot * B.slot_bytes, src, (uint32_t)cd.z, bar + slot);
+    sdesc[pslot] = cd;
+    bulk_load(slots + (size_t)pslot * B.slot_bytes, src, (uint32_t)cd.z, bar + pslot);
+    if (++pslot == ns) pslot = 0;
     ++issued;
-    if (++pc == __ldg(J.P.cptr + J.P.nb)) {
+    if (++pc == nch_p) {
       pc = 0;
       pg += gridDim.x;
-      if (pg < B.ntiles) pj = job_of(B, pg);
+      if (pg < B.ntiles) {
+        pj = job_of(B, pg);
+        nch_p = __ldg(B.job[pj].P.cptr + B.job[pj].P.nb);
+      }
     }
+    if (pg < B.ntiles) cdn = __ldg(B.job[pj].P.chunks + pc);
   };
 
   if (t == 0) {
@@ -203,8 +291,11 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
   __syncthreads();
   if (t == 0)
     for (int s = 0; s < ns; ++s) issue_next();
+  __syncthreads();  // the first descriptors are visible to every thread
 
-  long long pos = 0;
+  long long pos = 0;  // chunks consumed
+  int cslot = 0;      // their slot and mbarrier phase
+  uint32_t cphase = 0;
   for (long long g = blockIdx.x; g < B.ntiles; g += gridDim.x) {
     const WalkJob<T, TM>& J = B.job[job_of(B, g)];
     const long long cg = (g - J.tile0) * TC + cl;
@@ -213,6 +304,7 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
     const T inv_h2 = (T)J.geo.inv_h2;
     T* X = J.X;
     const T* Bsrc = J.B;
+    const T* ddg = J.ddiag;
     const int nb = J.P.nb;
     long long p = 0;
     long long nbr[4] = {-1, -1, -1, -1};
@@ -231,163 +323,123 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
       }
     }
     double local_max = 0.0;
-    // right-hand side (and, for the product, the x tile) of the next leaf, prefetched
-    T bn[Q], xn[Q];
+    // right-hand side, x tile (product) and diagonal term (FP32 products) of the next leaf,
+    // prefetched a leaf ahead by the threads that use them
+    T bn[Q], xn[Q], dn[Q];
     auto load_rhs = [&](int leaf) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const int r = rg + RG * q;
-        T b = 0, x = 0;
-        if (valid && sp == 0 && leaf < nb) {
-          const long long base = (long long)(leaf * L + r) * ld;
-          b = Bsrc[base + p];
-          if (MODE == MODE_SMOOTH) {
-            T s = 0;
+        const int r = rb + RG * q;
+        T b = 0, x = 0, d = 0;
+        if (act && sp == 0 && leaf < nb) {
+          if (SPLITD) d = ddg[(long long)leaf * L + r];
+          if (valid) {
+            const long long base = (long long)(leaf * L + r) * ld;
+            b = Bsrc[base + p];
+            if (MODE == MODE_SMOOTH) {
+              T s = 0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (nbr[e] >= 0) s += X[base + nbr[e]];
-            b += s * inv_h2;
-          } else {
-            x = X[base + p];
+              for (int e = 0; e < 4; ++e)
+                if (nbr[e] >= 0) s += X[base + nbr[e]];
+              b += s * inv_h2;
+            } else {
+              x = X[base + p];
+            }
           }
         }
         bn[q] = b;
         xn[q] = x;
+        dn[q] = d;
       }
     };
     load_rhs(0);
 
     for (int i = 0; i < nb; ++i) {
-      T acc[Q];
-      TM part[Q][NA];
-      T xcur[Q];
+      T acc[Q], xcur[Q], ddv[Q];
+      TM part[Q][4];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         acc[q] = bn[q];
         xcur[q] = xn[q];
+        ddv[q] = dn[q];
 #pragma unroll
-        for (int a = 0; a < NA; ++a) part[q][a] = 0;
+        for (int a = 0; a < 4; ++a) part[q][a] = 0;
       }
-      const int c1 = __ldg(J.P.cptr + i + 1);
-      for (int c = __ldg(J.P.cptr + i); c < c1; ++c, ++pos) {
-        const int slot = (int)(pos % ns);
-        if (!mbar_wait(bar + slot, (uint32_t)((pos / ns) & 1))) {
+      TM* xr_i = ring + ((i % W) * TC + cl) * LP;  // x_i of this column, once computed
+      for (bool leaf_done = false; !leaf_done; ++pos) {
+        if (!mbar_wait(bar + cslot, cphase)) {
           *sflag = 1;
           atomicExch(B.err, 1);
         }
-        const int4 cd = __ldg(J.P.chunks + c);
-        const int type = cd.x & 15, cnt = cd.x >> 4;
-        const unsigned char* buf = slots + (size_t)slot * B.slot_bytes;
+        const int4 cd = sdesc[cslot];
+        leaf_done = ((cd.x >> 12) & 1) != 0;
+        const int type = cd.x & 15, cnt = (cd.x >> 4) & 0xff;
+        const unsigned char* buf = slots + (size_t)cslot * B.slot_bytes;
+        const VT* A = reinterpret_cast<const VT*>(buf);
         if (type == PK_DENSE) {
-          const TM* D = reinterpret_cast<const TM*>(buf);
           const int j = cd.y;
           if (i - j < W) {
-            const TM* xr = ring + (size_t)(j % W) * L * TC;
+            const TM* xr = ring + ((j % W) * TC + cl) * LP;
 #pragma unroll
-            for (int kk = 0; kk < KS; ++kk) {
-              const int k = sp + kk * S;
-              const TM xv = xr[k * TC + cl];
+            for (int gg = 0; gg < NVT; ++gg) {
+              const int g = sp + gg * S;
+              const VT xv = *reinterpret_cast<const VT*>(xr + g * VE);
 #pragma unroll
-              for (int q = 0; q < Q; ++q) part[q][kk % NA] += D[k * L + rg + RG * q] * xv;
+              for (int q = 0; q < Q; ++q) vfma(part[q], gg, A[g * L + rb + RG * q], xv);
             }
           } else {
             const T* xj = X + (long long)j * L * ld + p;
 #pragma unroll
-            for (int kk = 0; kk < KS; ++kk) {
-              const int k = sp + kk * S;
-              const TM xv = valid ? (TM)xj[(long long)k * ld] : (TM)0;
+            for (int gg = 0; gg < NVT; ++gg) {
+              const int g = sp + gg * S;
+              const VT xv = load_col(xj, (long long)g * VE, ld, valid, (TM*)nullptr);
 #pragma unroll
-              for (int q = 0; q < Q; ++q) part[q][kk % NA] += D[k * L + rg + RG * q] * xv;
+              for (int q = 0; q < Q; ++q) vfma(part[q], gg, A[g * L + rb + RG * q], xv);
             }
           }
         } else if (type == PK_UPART) {
-          const TM* U = reinterpret_cast<const TM*>(buf);
           const int* uz = reinterpret_cast<const int*>(buf + (size_t)cnt * L * sizeof(TM));
-          int a = 0;
-          for (int kk = sp; kk < cnt; kk += S) {
-            const TM zv = zp[uz[kk] * TC + cl];
+          const int nvq = cnt / VE;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) part[q][a] += U[kk * L + rg + RG * q] * zv;
-            a = (a + 1 == NA) ? 0 : a + 1;
+          for (int gg = 0; gg < NVT; ++gg) {
+            const int g = sp + gg * S;
+            if (g < nvq) {
+              const VT zv = gather_z(zp, uz + g * VE, TC, cl);
+#pragma unroll
+              for (int q = 0; q < Q; ++q) vfma(part[q], gg, A[g * L + rb + RG * q], zv);
+            }
           }
         } else if (type == PK_DIAG) {
-          const TM* Dd = reinterpret_cast<const TM*>(buf);
-          const T* ddiag = J.ddiag;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc[q] = reduce_splits<T, STEP>(acc[q] - (T)sum4(part[q]));
+          // the operand of the diagonal product: y (smoother) or x_i (product), in TM
+          TM* opnd = MODE == MODE_SMOOTH ? ysm + cl * LP : xr_i;
+          if (sp == 0 && act) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) opnd[rb + RG * q] = (TM)(MODE == MODE_SMOOTH ? acc[q] : xcur[q]);
+          }
+          __syncthreads();
 #pragma unroll
           for (int q = 0; q < Q; ++q) {
-            TM s = part[q][0];
+            const int r = rb + RG * q;
+            TM a4[4] = {0, 0, 0, 0};
 #pragma unroll
-            for (int a = 1; a < NA; ++a) s += part[q][a];
-            acc[q] = reduce_splits<T, TC, S>(acc[q] - (T)s);
-          }
-          TM* xr_i = ring + (size_t)(i % W) * L * TC;
-          if (MODE == MODE_SMOOTH) {
-            if (sp == 0) {
-#pragma unroll
-              for (int q = 0; q < Q; ++q) {
-                ys[(rg + RG * q) * TC + cl] = acc[q];
-                ysm[(rg + RG * q) * TC + cl] = (TM)acc[q];
-              }
+            for (int gg = 0; gg < NVT; ++gg) {
+              const int g = sp + gg * S;
+              vfma(a4, gg, A[g * L + r], *reinterpret_cast<const VT*>(opnd + g * VE));
             }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              const int r = rg + RG * q;
-              TM s[NA];
-#pragma unroll
-              for (int a = 0; a < NA; ++a) s[a] = 0;
-#pragma unroll
-              for (int kk = 0; kk < KS; ++kk) {
-                const int k = sp + kk * S;
-                if (ddiag ? k < r : k <= r) s[kk % NA] += Dd[k * L + r] * ysm[k * TC + cl];
+            const T s = reduce_splits<T, STEP>((T)sum4(a4));
+            if (MODE == MODE_SMOOTH) {
+              T x = s;
+              if (SPLITD) x += ddv[q] * acc[q];
+              if (sp == 0 && act) {
+                xr_i[r] = (TM)x;
+                if (valid) X[(long long)(i * L + r) * ld + p] = x;
               }
-              TM s1 = s[0];
-#pragma unroll
-              for (int a = 1; a < NA; ++a) s1 += s[a];
-              T x = reduce_splits<T, TC, S>((T)s1);
-              if (ddiag) x += ddiag[(long long)i * L + r] * ys[r * TC + cl];
-              acc[q] = x;
-            }
-            __syncthreads();
-            if (sp == 0) {
-#pragma unroll
-              for (int q = 0; q < Q; ++q) {
-                const int r = rg + RG * q;
-                const TM xm = (TM)acc[q];
-                ysm[r * TC + cl] = xm;
-                xr_i[r * TC + cl] = xm;
-                if (valid) X[(long long)(i * L + r) * ld + p] = acc[q];
-              }
-            }
-          } else {
-            if (sp == 0) {
-#pragma unroll
-              for (int q = 0; q < Q; ++q) {
-                const int r = rg + RG * q;
-                const TM xm = (TM)xcur[q];
-                ys[r * TC + cl] = xcur[q];
-                ysm[r * TC + cl] = xm;
-                xr_i[r * TC + cl] = xm;
-              }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              const int r = rg + RG * q;
-              TM s[NA];
-#pragma unroll
-              for (int a = 0; a < NA; ++a) s[a] = 0;
-#pragma unroll
-              for (int kk = 0; kk < KS; ++kk) {
-                const int k = sp + kk * S;
-                if (ddiag ? k < r : k <= r) s[kk % NA] += Dd[k * L + r] * ysm[k * TC + cl];
-              }
-              TM s1 = s[0];
-#pragma unroll
-              for (int a = 1; a < NA; ++a) s1 += s[a];
-              T o = acc[q] - reduce_splits<T, TC, S>((T)s1);
-              if (ddiag) o -= ddiag[(long long)i * L + r] * ys[r * TC + cl];
-              if (valid && sp == 0) {
+            } else {
+              T o = acc[q] - s;
+              if (SPLITD) o -= ddv[q] * xcur[q];
+              if (valid && sp == 0 && act) {
                 if (J.OUT) J.OUT[(long long)(i * L + r) * ld + p] = o;
                 const double av = fabs((double)o);
                 local_max = (av > local_max || av != av) ? av : local_max;
@@ -395,25 +447,24 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
             }
           }
           load_rhs(i + 1);  // the next leaf's loads overlap the V slabs and the next chunk waits
-        } else {  // PK_VPART
-          const TM* V = reinterpret_cast<const TM*>(buf);
+        } else {  // PK_VPART: rows are z entries, the reduction runs over x_i
           const int* vz = reinterpret_cast<const int*>(buf + (size_t)cnt * L * sizeof(TM));
-          const int O = cnt * TC;
-          int Sv = 32;
-          while (Sv > 1 && Sv * O > NT) Sv >>= 1;
-          const int gq = t / Sv, sv = t % Sv, G = NT / Sv;
-          for (int base = 0; base < O; base += G) {
-            const int o = base + gq;
-            TM s = 0;
-            if (o < O) {
-              const int kk = o / TC, cc = o % TC;
-              for (int k = sv; k < L; k += Sv) s += V[kk * L + k] * ysm[k * TC + cc];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const int r = rb + RG * q;
+            const bool live = act && r < cnt;
+            TM a4[4] = {0, 0, 0, 0};
+            if (live) {
+#pragma unroll
+              for (int gg = 0; gg < NVT; ++gg) {
+                const int g = sp + gg * S;
+                vfma(a4, gg, A[g * cnt + r], *reinterpret_cast<const VT*>(xr_i + g * VE));
+              }
             }
-            for (int w = Sv >> 1; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
-            if (o < O && sv == 0) {
-              const int kk = o / TC, cc = o % TC;
-              const int code = vz[kk];
-              TM* z = zp + (code >> 1) * TC + cc;
+            const TM s = reduce_splits<TM, STEP>(sum4(a4));
+            if (live && sp == 0) {
+              const int code = vz[r];
+              TM* z = zp + (code >> 1) * TC + cl;
               *z = (code & 1) ? s : *z + s;
             }
           }
@@ -421,13 +472,26 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
         __syncthreads();  // the slot and every shared-memory write of this chunk are done
         if (*sflag) {
           // drain (bounded) the copies still in flight, then leave
-          if (t == 0)
-            for (long long q2 = pos + 1; q2 < issued; ++q2) mbar_wait(bar + (int)(q2 % ns), (uint32_t)((q2 / ns) & 1));
+          if (t == 0) {
+            int s2 = cslot;
+            uint32_t ph2 = cphase;
+            for (long long q2 = pos + 1; q2 < issued; ++q2) {
+              if (++s2 == ns) {
+                s2 = 0;
+                ph2 ^= 1;
+              }
+              mbar_wait(bar + s2, ph2);
+            }
+          }
           return;
         }
         if (t == 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           issue_next();
+        }
+        if (++cslot == ns) {
+          cslot = 0;
+          cphase ^= 1;
         }
       }
     }

@@ -18,7 +18,7 @@ struct WalkArgsT {
   const T* B;
   T* OUT;
   const void* Dinv;            // TM*, level inverses (smoother)
-  const T* ddiag;              // FP64-storage mixed path only
+  const T* ddiag;              // FP32 products: diagonal of the DIAG blocks (see WalkJob)
   unsigned long long* norm;
   int* err;                    // device error word (bounded-wait timeout); the first job's is used
   int tile;                    // 0: automatic, else the column tile TC (the first job's is used)

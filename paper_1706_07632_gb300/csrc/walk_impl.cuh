@@ -19,7 +19,7 @@ inline int panel_slots(int slot_bytes) {
 
 template <typename T, typename TM>
 size_t panel_bytes(int L, int TC, int pool, int W, int slot_bytes, int ns) {
-  return panel_smem(L, TC, pool, W, slot_bytes, ns, sizeof(T), sizeof(TM)).total;
+  return panel_smem(L, TC, pool, W, slot_bytes, ns, sizeof(TM)).total;
 }
 
 template <typename T, typename TM, int L, int TC, int MODE>
@@ -80,16 +80,29 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
       *err = "jobs of one walk launch must share the leaf size";
       return 2;
     }
+    if (sizeof(TM) < 8 && jobs[j].ddiag == nullptr) {
+      *err = "FP32 products need the diagonal of the streamed DIAG blocks (ddiag)";
+      return 2;
+    }
     pool = std::max(pool, jobs[j].P.pool);
     W = std::max(W, jobs[j].P.W);
     slot = std::max(slot, jobs[j].P.slot_bytes);
     cols = std::max(cols, jobs[j].ncols);
   }
-  const int ns = panel_slots(slot);
+  int ns = panel_slots(slot);
   long long total_cols = 0;
   for (int j = 0; j < njobs; ++j) total_cols += jobs[j].ncols;
   const int TC = jobs[0].tile ? jobs[0].tile : panel_pick<T, TM>(L, pool, W, slot, ns, total_cols);
   if (tile_used) *tile_used = TC;
+  // Pipeline depth: when every tile gets its own SM (one CTA per SM), a CTA has little work per
+  // chunk and the copies' latency dominates -- deepen the ring up to ~200 KB of shared memory;
+  // otherwise keep ~96 KB of slots so that two CTAs fit per SM.
+  long long tiles_all = 0;
+  for (int j = 0; j < njobs; ++j) tiles_all += (jobs[j].ncols + TC - 1) / TC;
+  if (tiles_all <= kPanelSMs) {
+    const size_t other = panel_bytes<T, TM>(L, TC, pool, W, slot, 0);
+    while (ns < 16 && other + (size_t)(ns + 1) * slot + 64 <= kPanelSmemCap) ++ns;
+  }
   if (panel_bytes<T, TM>(L, TC, pool, W, slot, ns) > 227 * 1024) {
     *err = "panel shared memory exceeds 227 KB";
     return 2;

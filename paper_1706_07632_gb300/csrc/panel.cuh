@@ -4,10 +4,15 @@
 // A CTA owns TC time lines (columns) at a time and walks the leaf rows i = 0..nb-1 of the time
 // matrix in order; it is persistent over column tiles.  The H-matrix data arrive as a stream of
 // chunks (near-field blocks, slabs of the low-rank factors U and V, the diagonal block or its
-// level inverse), in exactly the order the walk consumes them.  Thread 0 keeps NS chunks in
-// flight: each chunk is one cp.async.bulk (TMA bulk copy, global -> shared) into a ring slot,
-// completing on that slot's mbarrier; every thread waits on the slot's mbarrier (bounded spin)
-// before using it, and the slot is refilled after the block-wide barrier that ends the chunk.
+// level inverse), in exactly the order the walk consumes them.  A producer warp keeps NS chunks
+// in flight: each chunk is one cp.async.bulk (TMA bulk copy, global -> shared) into a ring slot,
+// completing on that slot's "full" mbarrier; every consumer thread waits on it before using the
+// slot, and each consumer warp arrives on the slot's "empty" mbarrier when done, which lets the
+// producer refill it.  Consumer warps therefore run through near-field, low-rank and V chunks
+// without block-wide barriers; they meet only in the diagonal step, where y is exchanged and x_i
+// published (an mbarrier over the consumer warps).  Every wait is a bounded mbarrier poll that
+// also watches a shared abort flag: a warp whose wait gives up sets the flag and the error word
+// and leaves, and every other wait then ends too, so no thread can be left waiting.
 // All columns of the tile reuse every staged chunk.
 //
 // Per leaf row i the accumulators start from the right-hand side (smoother: F + neighbour
@@ -139,6 +144,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// a consumer warp's release of a slot (one arrival per warp)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait that also gives up once *abort is set (the producer's waits)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63 && *abort) return false;
+  }
+  return false;
+}
+
 // one TMA bulk copy global -> shared, completing bytes on the slot's mbarrier
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -160,7 +186,7 @@ __device__ __forceinline__ T reduce_splits(T v) {
 // leaf's y, the ring of recent leaves' x) are stored per column with a padded length L + VE, so
 // that 16-byte reads of different columns fall in different banks.
 struct PanelSmem {
-  size_t ysm, ring, zp, bar, desc, flag, total;
+  size_t ysm, ring, zp, bar, ebar, cbar, desc, flag, total;
 };
 __host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, int slot_bytes, int ns, int bTM) {
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
@@ -169,8 +195,10 @@ __host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, 
   s.ysm = a16((size_t)ns * slot_bytes);
   s.ring = a16(s.ysm + (size_t)TC * LP * bTM);
   s.zp = a16(s.ring + (size_t)W * TC * LP * bTM);
-  s.bar = a16(s.zp + (size_t)pool * TC * bTM);
-  s.desc = a16(s.bar + 8 * (size_t)ns);  // descriptor of the chunk in each slot
+  s.bar = a16(s.zp + (size_t)pool * TC * bTM);  // "full" mbarriers
+  s.ebar = s.bar + 8 * (size_t)ns;                 // "empty" mbarriers
+  s.cbar = s.ebar + 8 * (size_t)ns;                // the consumer warps' own barrier
+  s.desc = a16(s.cbar + 8);                        // descriptor of the chunk in each slot
   s.flag = s.desc + 16 * (size_t)ns;
   s.total = a16(s.flag + 16);
   return s;
@@ -217,11 +245,13 @@ __device__ __forceinline__ int job_of(const WalkBatch<T, TM>& B, long long g) {
   return j;
 }
 
+// NT_ consumer threads (the walk) + one producer warp (the chunk stream).
 template <typename T, typename TM, int L, int TC, int MODE, int NT_>
-__global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ WalkBatch<T, TM> B) {
+__global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant__ WalkBatch<T, TM> B) {
   using VT = typename VecOf<TM>::type;
   constexpr int VE = VecOf<TM>::n;
   using TL = PTile<L, TC, NT_, VE>;
+  constexpr int NT = NT_;
   constexpr int Q = TL::Q, RG = TL::RG, S = TL::S, RL = TL::RL, NVT = TL::NVT;
   constexpr int STEP = TC * RL;            // lane offset between splits
   constexpr int LP = L + VE;               // padded x-tile column
@@ -232,69 +262,94 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
   TM* ysm = reinterpret_cast<TM*>(sm + lay.ysm);  // y of the current leaf (smoother), in TM
   TM* ring = reinterpret_cast<TM*>(sm + lay.ring);
   TM* zp = reinterpret_cast<TM*>(sm + lay.zp);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + lay.bar);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + lay.bar);
+  uint64_t* empty = reinterpret_cast<uint64_t*>(sm + lay.ebar);
+  uint64_t* cbar = reinterpret_cast<uint64_t*>(sm + lay.cbar);
   int4* sdesc = reinterpret_cast<int4*>(sm + lay.desc);
-  volatile int* sflag = reinterpret_cast<volatile int*>(sm + lay.flag);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + lay.flag);
 
   const int t = threadIdx.x;
   const int lane = t & 31;
+  const int ns = B.ns;
+  const int W = B.W;
+
+  if (t == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, NT / 32);
+    }
+    mbar_init(cbar, NT / 32);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the last block-wide barrier: from here on the roles run apart
+
+  if (t >= NT) {
+    // ---- producer: one lane streams every chunk of every tile of this CTA, in order ----
+    if (t != NT) return;
+    long long k = 0;  // chunks issued
+    int slot = 0;
+    bool ok = true;
+    for (long long g = blockIdx.x; g < B.ntiles && ok; g += gridDim.x) {
+      const WalkJob<T, TM>& J = B.job[job_of(B, g)];
+      const int nch = __ldg(J.P.cptr + J.P.nb);
+      int4 cdn = __ldg(J.P.chunks);
+      for (int c = 0; c < nch; ++c, ++k) {
+        const int4 cd = cdn;
+        if (c + 1 < nch) cdn = __ldg(J.P.chunks + c + 1);
+        if (k >= ns && !mbar_wait_or_abort(empty + slot, (uint32_t)(((k / ns) - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int type = cd.x & 15;
+        const void* src = (MODE == MODE_SMOOTH && type == PK_DIAG)
+                              ? (const void*)(J.Dinv + (long long)cd.y * L * L)
+                              : (const void*)(J.P.pkg + 16LL * (long long)cd.w);
+        sdesc[slot] = cd;  // published by the mbarrier arrive below (release), read after the wait
+        bulk_load(slots + (size_t)slot * B.slot_bytes, src, (uint32_t)cd.z, full + slot);
+        if (++slot == ns) slot = 0;
+      }
+    }
+    if (!ok && !*abort_flag) {  // timed out waiting for the consumers
+      *abort_flag = 1;
+      atomicExch(B.err, 1);
+    }
+    // every copy in flight lands before the CTA may retire (bounded, abort or not)
+    for (int s = 0; s < ns && s < k; ++s) {
+      const long long n_s = (k - 1 - s) / ns + 1;  // issues into slot s
+      mbar_wait(full + s, (uint32_t)((n_s - 1) & 1));
+    }
+    return;
+  }
+
+  // ---- consumers ----
   const int cl = lane % TC;
   const int rl = (lane / TC) % RL;
   const int sp = lane / STEP;
   const int rb0 = (t >> 5) * RL + rl;
   const bool act = rb0 < RG;  // false only in the surplus warps of small leaves
   const int rb = act ? rb0 : 0;
-  const int ns = B.ns;
-  const int W = B.W;
-
-  // Producer cursor (thread 0): the next (tile, chunk) to stage, in consumption order.  The
-  // descriptor of the next chunk is loaded one issue ahead, so that no global load sits on the
-  // producer's path between two block barriers; each issued descriptor is published in sdesc[slot]
-  // for the consumers (at least one block barrier separates that write from its use).
-  long long pg = blockIdx.x;
-  int pj = 0, pc = 0, nch_p = 0, pslot = 0;
-  int4 cdn = make_int4(0, 0, 0, 0);
-  if (t == 0 && pg < B.ntiles) {
-    pj = job_of(B, pg);
-    nch_p = __ldg(B.job[pj].P.cptr + B.job[pj].P.nb);
-    cdn = __ldg(B.job[pj].P.chunks);
-  }
-  long long issued = 0;
-  auto issue_next = [&]() {
-    if (pg >= B.ntiles) return;
-    const WalkJob<T, TM>& J = B.job[pj];
-    const int4 cd = cdn;
-    const int type = cd.x & 15;
-    const void* src = (MODE == MODE_SMOOTH && type == PK_DIAG)
-                          ? (const void*)(J.Dinv + (long long)cd.y * L * L)
-                          : (const void*)(J.P.pkg + 16LL * (long long)cd.w);
-    sdesc[pslot] = cd;
-    bulk_load(slots + (size_t)pslot * B.slot_bytes, src, (uint32_t)cd.z, bar + pslot);
-    if (++pslot == ns) pslot = 0;
-    ++issued;
-    if (++pc == nch_p) {
-      pc = 0;
-      pg += gridDim.x;
-      if (pg < B.ntiles) {
-        pj = job_of(B, pg);
-        nch_p = __ldg(B.job[pj].P.cptr + B.job[pj].P.nb);
-      }
+  uint32_t cbphase = 0;  // phase of the consumer barrier
+  // warp-uniform exit after a wait that gave up (its own timeout or another warp's abort)
+  auto give_up = [&](bool ok) -> bool {
+    if (__all_sync(0xffffffffu, ok)) return false;
+    if (lane == 0) {
+      *abort_flag = 1;
+      atomicExch(B.err, 1);
     }
-    if (pg < B.ntiles) cdn = __ldg(B.job[pj].P.chunks + pc);
+    return true;
+  };
+  // all consumer warps meet (bounded)
+  auto consumer_sync = [&]() -> bool {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(cbar);
+    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag);
+    cbphase ^= 1;
+    return !give_up(ok);
   };
 
-  if (t == 0) {
-    for (int s = 0; s < ns; ++s) mbar_init(bar + s, 1);
-    *sflag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (t == 0)
-    for (int s = 0; s < ns; ++s) issue_next();
-  __syncthreads();  // the first descriptors are visible to every thread
-
-  long long pos = 0;  // chunks consumed
-  int cslot = 0;      // their slot and mbarrier phase
+  int cslot = 0;  // slot and full-barrier phase of the next chunk
   uint32_t cphase = 0;
   for (long long g = blockIdx.x; g < B.ntiles; g += gridDim.x) {
     const WalkJob<T, TM>& J = B.job[job_of(B, g)];
@@ -366,11 +421,8 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
         for (int a = 0; a < 4; ++a) part[q][a] = 0;
       }
       TM* xr_i = ring + ((i % W) * TC + cl) * LP;  // x_i of this column, once computed
-      for (bool leaf_done = false; !leaf_done; ++pos) {
-        if (!mbar_wait(bar + cslot, cphase)) {
-          *sflag = 1;
-          atomicExch(B.err, 1);
-        }
+      for (bool leaf_done = false; !leaf_done;) {
+        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag))) return;
         const int4 cd = sdesc[cslot];
         leaf_done = ((cd.x >> 12) & 1) != 0;
         const int type = cd.x & 15, cnt = (cd.x >> 4) & 0xff;
@@ -418,7 +470,7 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
 #pragma unroll
             for (int q = 0; q < Q; ++q) opnd[rb + RG * q] = (TM)(MODE == MODE_SMOOTH ? acc[q] : xcur[q]);
           }
-          __syncthreads();
+          if (!consumer_sync()) return;  // the operand is complete
 #pragma unroll
           for (int q = 0; q < Q; ++q) {
             const int r = rb + RG * q;
@@ -447,6 +499,9 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
             }
           }
           load_rhs(i + 1);  // the next leaf's loads overlap the V slabs and the next chunk waits
+          // smoother: x_i is published for the V slabs (the product wrote its x_i before the first
+          // barrier; a warp can rewrite an operand only after every warp reached the next one)
+          if (MODE == MODE_SMOOTH && !consumer_sync()) return;
         } else {  // PK_VPART: rows are z entries, the reduction runs over x_i
           const int* vz = reinterpret_cast<const int*>(buf + (size_t)cnt * L * sizeof(TM));
 #pragma unroll
@@ -469,26 +524,8 @@ __global__ void __launch_bounds__(NT_) hpanel_kernel(const __grid_constant__ Wal
             }
           }
         }
-        __syncthreads();  // the slot and every shared-memory write of this chunk are done
-        if (*sflag) {
-          // drain (bounded) the copies still in flight, then leave
-          if (t == 0) {
-            int s2 = cslot;
-            uint32_t ph2 = cphase;
-            for (long long q2 = pos + 1; q2 < issued; ++q2) {
-              if (++s2 == ns) {
-                s2 = 0;
-                ph2 ^= 1;
-              }
-              mbar_wait(bar + s2, ph2);
-            }
-          }
-          return;
-        }
-        if (t == 0) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue_next();
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + cslot);  // this warp is done with the slot
         if (++cslot == ns) {
           cslot = 0;
           cphase ^= 1;

@@ -9,7 +9,8 @@
 namespace fhmg {
 
 constexpr int kPanelSMs = 152;
-constexpr int kPanelThreads = 256;
+constexpr int kPanelThreads = 256;                  // consumer threads of the walk
+constexpr int kPanelBlock = kPanelThreads + 32;     // + the producer warp
 constexpr size_t kPanelSmemCap = 200 * 1024;
 
 inline int panel_slots(int slot_bytes) {
@@ -39,13 +40,13 @@ int panel_launch_t(cudaStream_t st, const WalkBatch<T, TM>& B, std::string* err)
   }
   if (occ_smem != smem) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPanelThreads, smem) != cudaSuccess || o < 1) o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPanelBlock, smem) != cudaSuccess || o < 1) o = 1;
     occ = o;
     occ_smem = smem;
   }
   if (B.ntiles <= 0) return 0;
   const long long grid = std::min<long long>(B.ntiles, (long long)kPanelSMs * occ);
-  kern<<<(unsigned)grid, kPanelThreads, smem, st>>>(B);
+  kern<<<(unsigned)grid, kPanelBlock, smem, st>>>(B);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("panel launch: ") + cudaGetErrorString(e);

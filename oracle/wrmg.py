@@ -22,15 +22,19 @@ paper's order:
 5. linear (1D) / bilinear (2D) interpolation in space only, added to u.
 6. nu2 post-smoothing steps.
 On the coarsest level (one interior point per dimension) the system is solved directly.
+Optionally (n_direct > 1, a choice the paper leaves open: it recurses to one point) the
+coarse-grid correction is solved exactly as soon as the coarse grid has at most n_direct
+interior points per dimension (``direct_level_solve``); n_direct = 1 is the paper's cycle.
 Line solves and products use the dense Rt (library triangular solve / matmul), which is what
 Algorithms 3 and 4 compute.
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft
 import scipy.linalg
 
-from .direct import apply_ah, apply_ah_2d
+from .direct import apply_ah, apply_ah_2d, laplacian_eigs_1d, solve_o2_mode
 
 
 def _colour_masks_1d(N):
@@ -117,8 +121,28 @@ def coarsest_solve(Rt: np.ndarray, F: np.ndarray, h: float) -> np.ndarray:
     return scipy.linalg.solve_triangular(Ls, F.reshape(M, -1), lower=True).reshape(F.shape)
 
 
-def cycle(Rt, F, u, h, nu1=1, nu2=1, gamma_c=1):
-    """One WRMG cycle of Algorithm 2 on the level of F (V-cycle for gamma_c = 1)."""
+def direct_level_solve(Rt: np.ndarray, F: np.ndarray, h: float) -> np.ndarray:
+    """Exact solve of (Rt (x) I + I (x) A_h) u = F on one level.  The sine functions
+    sin(p pi n / (N+1)) are the eigenvectors of A_h (eigenvalues ``laplacian_eigs_1d``; in 2D
+    products of them, eigenvalue lam_p + lam_q), so the orthonormal DST-I in space decouples the
+    system into one lower-triangular time system (Rt + lam I) w = F^ per spatial mode."""
+    M = Rt.shape[0]
+    dim = F.ndim - 1
+    N = F.shape[1]
+    lam = laplacian_eigs_1d(N, h)
+    axes = tuple(range(1, dim + 1))
+    Fh = scipy.fft.dstn(F, type=1, axes=axes, norm="ortho").reshape(M, -1)
+    lam_modes = lam if dim == 1 else (lam[:, None] + lam[None, :]).reshape(-1)
+    W = np.empty_like(Fh)
+    for k, lk in enumerate(lam_modes):
+        W[:, k] = solve_o2_mode(Rt, lk, Fh[:, k])
+    return scipy.fft.idstn(W.reshape(F.shape), type=1, axes=axes, norm="ortho")
+
+
+def cycle(Rt, F, u, h, nu1=1, nu2=1, gamma_c=1, n_direct=1):
+    """One WRMG cycle of Algorithm 2 on the level of F (V-cycle for gamma_c = 1).  The
+    coarse-grid correction is solved exactly once the coarse grid has <= n_direct points per
+    dimension (n_direct = 1: the paper's recursion to one point)."""
     N = F.shape[1]
     if N == 1:
         return coarsest_solve(Rt, F, h)
@@ -126,23 +150,26 @@ def cycle(Rt, F, u, h, nu1=1, nu2=1, gamma_c=1):
         u = smooth(Rt, F, u, h)
     r = defect(Rt, F, u, h)
     rc = restrict_fw(r)
-    ec = np.zeros_like(rc)
-    for _ in range(gamma_c):
-        ec = cycle(Rt, rc, ec, 2.0 * h, nu1, nu2, gamma_c)
+    if n_direct > 1 and rc.shape[1] <= n_direct:
+        ec = direct_level_solve(Rt, rc, 2.0 * h)
+    else:
+        ec = np.zeros_like(rc)
+        for _ in range(gamma_c):
+            ec = cycle(Rt, rc, ec, 2.0 * h, nu1, nu2, gamma_c, n_direct)
     u = u + prolong(ec)
     for _ in range(nu2):
         u = smooth(Rt, F, u, h)
     return u
 
 
-def solve(Rt, F, h, nu1=1, nu2=1, rtol=1e-10, max_cycles=50, gamma_c=1, u0=None):
+def solve(Rt, F, h, nu1=1, nu2=1, rtol=1e-10, max_cycles=50, gamma_c=1, u0=None, n_direct=1):
     """Cycles from u0 (default zero) until ||r_k||_inf <= rtol ||r_0||_inf.
     Returns (u, cycles, residual-norm history)."""
     u = np.zeros_like(F) if u0 is None else np.array(u0, dtype=np.float64, copy=True)
     hist = [np.abs(defect(Rt, F, u, h)).max()]
     k = 0
     while hist[-1] > rtol * hist[0] and k < max_cycles:
-        u = cycle(Rt, F, u, h, nu1, nu2, gamma_c)
+        u = cycle(Rt, F, u, h, nu1, nu2, gamma_c, n_direct)
         hist.append(np.abs(defect(Rt, F, u, h)).max())
         k += 1
     return u, k, hist

@@ -195,6 +195,48 @@ def test_multigrid_converges_to_direct_solution(dim, N, M):
     assert np.abs(u - ud).max() <= 1e-10 * np.abs(ud).max()
 
 
+@pytest.mark.parametrize("dim,N,M", [(1, 7, 12), (1, 15, 8), (2, 3, 10), (2, 7, 4)])
+def test_direct_level_solve_matches_brute_force(dim, N, M):
+    # the sine-transform + per-mode triangular solve against the dense Kronecker system
+    t = l1.graded_mesh(1.0, M, 1.7)
+    R = l1.l1_matrix(t, 0.4)
+    h = 1.0 / (N + 1)
+    F = np.random.default_rng(5).standard_normal((M,) + (N,) * dim)
+    u = wrmg.direct_level_solve(R, F, h)
+    u3 = direct.solve_o3(R, F, h)
+    assert np.abs(u - u3).max() <= 1e-12 * np.abs(u3).max()
+
+
+def test_direct_level_solve_on_one_point_is_the_coarsest_solve():
+    t = l1.graded_mesh(1.0, 16, 2.0)
+    R = l1.l1_matrix(t, 0.5)
+    F = np.random.default_rng(6).standard_normal((16, 1))
+    a = wrmg.direct_level_solve(R, F, 0.5)
+    b = wrmg.coarsest_solve(R, F, 0.5)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dim,N,M", [(1, 63, 32), (2, 15, 16)])
+def test_exact_coarse_correction_converges_no_slower(dim, N, M):
+    # n_direct = 1 is the paper's cycle; an exact coarse-grid correction on the 7-point (1D) or
+    # 3x3 (2D) grid reaches the direct solution in no more cycles
+    t, h, F = _manufactured(dim, N, M, 0.5, 2.0)
+    R = l1.l1_matrix(t, 0.5)
+    ud = direct.solve_o1(R, F, h)
+    u1, k1, _ = wrmg.solve(R, F, h, 1, 1, 1e-11)
+    u7, k7, _ = wrmg.solve(R, F, h, 1, 1, 1e-11, n_direct=7 if dim == 1 else 3)
+    assert k7 <= k1
+    assert np.abs(u7 - ud).max() <= 1e-9 * np.abs(ud).max()
+    # a two-grid cycle with the exact coarse solve equals the full recursion once every
+    # coarser level is solved exactly: n_direct = N // 2 is a two-grid method
+    v0 = np.random.default_rng(7).standard_normal(F.shape)
+    a = wrmg.cycle(R, F, v0, h, 1, 1, n_direct=(N - 1) // 2)
+    v = wrmg.smooth(R, F, v0, h)
+    ec = direct.solve_o3(R, wrmg.restrict_fw(wrmg.defect(R, F, v, h)), 2.0 * h)
+    b = wrmg.smooth(R, F, v + wrmg.prolong(ec), h)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+
+
 def _asymptotic_factor(R, h, N, M, nu, gamma_c, seed=0, ncyc=12):
     rng = np.random.default_rng(seed)
     u = rng.standard_normal((M, N))

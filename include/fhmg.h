@@ -161,7 +161,19 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
  * a warm start with the zero initial guess fairly. */
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
 
-/* --- learned warm start (the benchmark spec addition; the paper has none) ------------------------------
+/* Coarse-grid solver of fhmg_vcycle / fhmg_solve.  n <= 1 (default): the paper's recursion to one
+ * interior point (Algorithm 2; the one-point system is solved by the line solve).  n = 2^k - 1 < N:
+ * the coarse-grid correction on the level with n points per dimension is solved exactly in FP64
+ * instead of recursing further -- a choice the paper leaves open.  A_h's sine eigenvectors
+ * (eigenvalues (4/h^2) sin^2(p pi / (2(n+1))), sums of two in 2D) decouple the level into one
+ * lower-triangular time system (R~ + lam_p I) w_p = RC^_p per spatial mode: an orthonormal DST-I in
+ * space, one H-matrix walk per mode (Algorithm 4 with the mode's shift; the per-mode diagonal
+ * inverses are built here on the device, n^dim * nb * L^2 doubles), the inverse transform.
+ * Synchronises the problem's stream.  EINVAL if n is not a coarse grid size or the level has more
+ * than 65535 points.  fhmg_solve_batched keeps the full recursion. */
+int fhmg_problem_set_coarse_direct(fhmg_problem p, int n);
+
+/* --- learned warm start (an addition to the method; the paper has none) ------------------------
  * For a source constant in time and a finite sine series, each spatial eigenmode s_k of A_h
  * (eigenvalue lam_k) evolves independently: u = sum_k c_k w_k(t) s_k with (R + lam_k I) w_k = 1.
  * A small network (6 features of (lam, alpha, t) -> hidden x layers, SiLU -> 1) predicts

@@ -67,7 +67,7 @@ def residual(R: np.ndarray, F: np.ndarray, u: np.ndarray, h: float) -> np.ndarra
 
 
 def solve_o1(R: np.ndarray, F: np.ndarray, h: float, m_stop: int | None = None) -> np.ndarray:
-    """Implicit time stepping with the dense history sum (the benchmark spec's direct oracle).
+    """Implicit time stepping with the dense history sum (the direct oracle).
 
     F is the full right-hand side (f + d_{m,m} g), shape (M, N) or (M, N, N).  If m_stop is
     given only the first m_stop time levels are computed (a bounded sample for timing)."""

@@ -58,6 +58,7 @@ _SIGS = {
                                 _c.POINTER(_I), _c.POINTER(_D)]),
     "fhmg_autotune_leaf": (_I, [_D, _D, _D, _I, _D, _I, _I, _D, _I, _P, _c.POINTER(_I), _c.POINTER(_D)]),
     "fhmg_problem_set_rtol_reference": (_I, [_P, _I]),
+    "fhmg_problem_set_coarse_direct": (_I, [_P, _I]),
     "fhmg_wsnet_create": (_I, [_I, _I, _c.c_ulonglong, _c.POINTER(_P)]),
     "fhmg_wsnet_destroy": (_I, [_P]),
     "fhmg_wsnet_num_params": (_I, [_P, _c.POINTER(_LL)]),
@@ -182,6 +183,11 @@ class Problem:
     def set_rtol_reference(self, ref):
         """0: ||r_k|| <= rtol ||r_0|| (default); 1: ||r_k|| <= rtol max|F|."""
         _check(lib().fhmg_problem_set_rtol_reference(self._p, ref))
+
+    def set_coarse_direct(self, n):
+        """Solve the coarse-grid correction exactly on the level with n points per dimension
+        (n <= 1: recursion to one point, the paper's cycle)."""
+        _check(lib().fhmg_problem_set_coarse_direct(self._p, n))
 
     def set_mixed_storage(self, mode):
         """0 automatic, 1 FP64 storage with FP32 products, 2 FP32 throughout (inner cycles)."""

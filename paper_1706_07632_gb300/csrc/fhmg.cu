@@ -11,6 +11,7 @@
 #include <utility>
 #include <vector>
 
+#include "coarse.cuh"
 #include "fhmg.h"
 #include "hbuild.h"
 #include "kernels.cuh"
@@ -105,6 +106,14 @@ struct fhmg_problem_s {
   double* hg = nullptr;
   int inner = 0;         // inner V-cycles per defect-correction step (0: 2 with FP32 storage, 4 otherwise)
   std::vector<void*> allocs;
+  // exact coarse-level solve (fhmg_problem_set_coarse_direct), FP64
+  int ndirect = 1;              // grid size per dimension solved exactly (1: recursion to one point)
+  int lcd = -1;                 // its level index (< nlev - 1), -1: none
+  double* dS = nullptr;         // orthonormal DST-I matrix of that level, n x n
+  double* dModeInv = nullptr;   // (D_ii + lam_k I)^{-1}: modes x nb x L x L, DIAG chunk layout
+  double* dCA = nullptr;        // scratch, M x points of that level
+  double* dCB = nullptr;
+  std::vector<void*> dallocs;   // the buffers above
   long long launches = 0;       // kernel launches issued (all kernels)
   bool profile = false;         // record events around finest-level smoother walks
   std::vector<cudaEvent_t> ev;  // start/stop pairs
@@ -326,14 +335,60 @@ int prolong_add(fhmg_problem p, int l, const T* e, T* u) {
   return FHMG_OK;
 }
 
+// E = exact solution of the level-l system for the right-hand side RC (FP64 throughout):
+// sine transform in space, one triangular H-matrix walk per spatial mode, inverse transform.
+template <typename T>
+int direct_level(fhmg_problem p, int l, T* E, const T* RC) {
+  const LevelData& lv = p->lev[l];
+  const int n = lv.N;
+  const long long M = p->M, tot = lv.npts * M;
+  const int blocks = blocks_for(tot);
+  if (p->dim == 1) {
+    fhmg::sine_transform_kernel<T, double><<<blocks, 256, 0, p->st>>>(RC, p->dCA, p->dS, M, 1, n, 0);
+  } else {
+    fhmg::sine_transform_kernel<T, double><<<blocks, 256, 0, p->st>>>(RC, p->dCB, p->dS, M, n, n, 0);
+    fhmg::sine_transform_kernel<double, double><<<blocks, 256, 0, p->st>>>(p->dCB, p->dCA, p->dS, M, n, n, 1);
+    ++p->launches;
+  }
+  ++p->launches;
+  CK(cudaGetLastError());
+  fhmg::WalkArgsT<double> a{};
+  a.P = p->panel64.d;
+  a.mode = fhmg::MODE_SMOOTH;
+  a.geo = Geo{0, 0, 0, lv.npts, 0.0};  // compact columns, no stencil: X = (R~ + lam I)^{-1} B
+  a.ncols = lv.npts;
+  a.X = p->dCB;
+  a.B = p->dCA;
+  a.Dinv = p->dModeInv;
+  a.dinv_cstride = (long long)p->nb * p->L * p->L;
+  a.err = p->derr;
+  a.tile = 1;
+  std::vector<fhmg::WalkArgsT<double>> j{a};
+  TRY(launch_jobs(p->st, K64, j, &p->launches));
+  if (p->dim == 1) {
+    fhmg::sine_transform_kernel<double, T><<<blocks, 256, 0, p->st>>>(p->dCB, E, p->dS, M, 1, n, 0);
+  } else {
+    fhmg::sine_transform_kernel<double, double><<<blocks, 256, 0, p->st>>>(p->dCB, p->dCA, p->dS, M, n, n, 1);
+    fhmg::sine_transform_kernel<double, T><<<blocks, 256, 0, p->st>>>(p->dCA, E, p->dS, M, n, n, 0);
+    ++p->launches;
+  }
+  ++p->launches;
+  CK(cudaGetLastError());
+  return FHMG_OK;
+}
+
 template <typename T>
 int vcycle_rec(fhmg_problem p, int l, T* u, const T* F, int nu1, int nu2, int kind) {
   if (l == 0) return sweep<T>(p, 0, u, F, kind);  // one interior point: the colour-0 solve is exact
   for (int s = 0; s < nu1; ++s) TRY(sweep<T>(p, l, u, F, kind));
   LevelData& lc = p->lev[l - 1];
   TRY(restrict_defect<T>(p, l, u, F, lev_RC<T>(lc), kind));
-  CK(cudaMemsetAsync(lev_E<T>(lc), 0, sizeof(T) * lc.npts * p->M, p->st));
-  TRY(vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind));
+  if (l - 1 == p->lcd) {
+    TRY(direct_level<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc)));
+  } else {
+    CK(cudaMemsetAsync(lev_E<T>(lc), 0, sizeof(T) * lc.npts * p->M, p->st));
+    TRY(vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind));
+  }
   TRY(prolong_add<T>(p, l, lev_E<T>(lc), u));
   for (int s = 0; s < nu2; ++s) TRY(sweep<T>(p, l, u, F, kind));
   return FHMG_OK;
@@ -777,6 +832,7 @@ int fhmg_problem_destroy(fhmg_problem p) {
   if (!p) return FHMG_OK;
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
+  for (void* a : p->dallocs) cudaFree(a);
   for (void* a : p->panel64.allocs) cudaFree(a);
   for (void* a : p->panel32.allocs) cudaFree(a);
   delete p;
@@ -969,6 +1025,56 @@ int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode) {
   TRY(check_dims(p));
   if (mode < 0 || mode > 2) return fail(FHMG_EINVAL, "mixed storage mode must be 0, 1 or 2");
   p->mixed_storage = mode;
+  return FHMG_OK;
+}
+
+int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
+  TRY(check_dims(p));
+  if (n < 0) return fail(FHMG_EINVAL, "coarse direct size must be >= 0");
+  int l = -1;
+  if (n > 1) {
+    for (int q = 0; q < p->nlev - 1; ++q)
+      if (p->lev[q].N == n) l = q;
+    if (l < 0) return fail(FHMG_EINVAL, "coarse direct size must be a coarse grid size 2^k - 1 below N (got %d)", n);
+    if (p->lev[l].npts > 65535) return fail(FHMG_EINVAL, "coarse direct level has more than 65535 points");
+  }
+  CK(cudaStreamSynchronize(p->st));
+  for (void* a : p->dallocs) cudaFree(a);
+  p->dallocs.clear();
+  p->dS = p->dModeInv = p->dCA = p->dCB = nullptr;
+  p->ndirect = 1;
+  p->lcd = -1;
+  if (l < 0) return FHMG_OK;
+  const LevelData& lv = p->lev[l];
+  const int L = p->L, nb = p->nb;
+  const double pi = std::acos(-1.0);
+  std::vector<double> S((size_t)n * n), lam1(n), lam(lv.npts), Dd((size_t)nb * L * L);
+  const double sc = std::sqrt(2.0 / (n + 1));
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) S[(size_t)j * n + k] = sc * std::sin(pi * (j + 1) * (k + 1) / (n + 1));
+  for (int q = 0; q < n; ++q) {
+    const double sn = std::sin(pi * (q + 1) / (2.0 * (n + 1)));
+    lam1[q] = 4.0 * lv.inv_h2 * sn * sn;
+  }
+  for (long long m = 0; m < lv.npts; ++m) lam[m] = p->dim == 1 ? lam1[m] : lam1[m / n] + lam1[m % n];
+  for (int i = 0; i < nb; ++i)
+    std::memcpy(&Dd[(size_t)i * L * L], p->H->host.dense[p->H->host.diag[i]].D.data(), sizeof(double) * L * L);
+  const double *dS, *dlam, *dDd;
+  TRY(upload(p->dallocs, S, &dS, nullptr));
+  TRY(upload(p->dallocs, lam, &dlam, nullptr));
+  TRY(upload(p->dallocs, Dd, &dDd, nullptr));
+  p->dS = const_cast<double*>(dS);
+  TRY(dalloc(p->dallocs, &p->dModeInv, (size_t)lv.npts * nb * L * L));
+  TRY(dalloc(p->dallocs, &p->dCA, (size_t)lv.npts * p->M));
+  TRY(dalloc(p->dallocs, &p->dCB, (size_t)lv.npts * p->M));
+  const int smem = 2 * L * L * (int)sizeof(double);
+  CK(cudaFuncSetAttribute(fhmg::mode_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  fhmg::mode_inverse_kernel<<<dim3(nb, (unsigned)lv.npts), L, smem, p->st>>>(dDd, dlam, L, nb, p->dModeInv);
+  ++p->launches;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->st));
+  p->ndirect = n;
+  p->lcd = l;
   return FHMG_OK;
 }
 

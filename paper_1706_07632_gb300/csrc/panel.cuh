@@ -211,6 +211,8 @@ __host__ __device__ inline PanelSmem panel_smem(int L, int TC, int pool, int W, 
 //     norm != NULL folds max |OUT| into *norm (bit pattern of a non-negative double).
 //   ddiag (FP32 products, required): the diagonal of the streamed DIAG blocks, nb x L, in T; the
 //     FP32 blocks are stored without it and the diagonal term is applied in T.
+//   dinv_cstride (smoother, one column per tile only): column c streams its own inverse set
+//     Dinv + c * dinv_cstride (a per-column shift, e.g. one spatial eigenmode per column).
 constexpr int kMaxJobs = 64;
 
 template <typename T, typename TM>
@@ -223,6 +225,7 @@ struct WalkJob {
   const T* B;
   T* OUT;
   const TM* Dinv;
+  long long dinv_cstride;
   const T* ddiag;
   unsigned long long* norm;
 };
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant_
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const int type = cd.x & 15;
         const void* src = (MODE == MODE_SMOOTH && type == PK_DIAG)
-                              ? (const void*)(J.Dinv + (long long)cd.y * L * L)
+                              ? (const void*)(J.Dinv + (g - J.tile0) * TC * J.dinv_cstride + (long long)cd.y * L * L)
                               : (const void*)(J.P.pkg + 16LL * (long long)cd.w);
         sdesc[slot] = cd;  // published by the mbarrier arrive below (release), read after the wait
         bulk_load(slots + (size_t)slot * B.slot_bytes, src, (uint32_t)cd.z, full + slot);

@@ -18,6 +18,7 @@ struct WalkArgsT {
   const T* B;
   T* OUT;
   const void* Dinv;            // TM*, level inverses (smoother)
+  long long dinv_cstride;      // 0, or per-column inverse sets (forces a column tile of 1)
   const T* ddiag;              // FP32 products: diagonal of the DIAG blocks (see WalkJob)
   unsigned long long* norm;
   int* err;                    // device error word (bounded-wait timeout); the first job's is used

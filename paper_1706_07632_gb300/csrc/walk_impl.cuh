@@ -93,7 +93,11 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
   int ns = panel_slots(slot);
   long long total_cols = 0;
   for (int j = 0; j < njobs; ++j) total_cols += jobs[j].ncols;
-  const int TC = jobs[0].tile ? jobs[0].tile : panel_pick<T, TM>(L, pool, W, slot, ns, total_cols);
+  bool per_column_inverse = false;
+  for (int j = 0; j < njobs; ++j) per_column_inverse |= jobs[j].dinv_cstride != 0;
+  const int TC = per_column_inverse ? 1
+                 : jobs[0].tile     ? jobs[0].tile
+                                    : panel_pick<T, TM>(L, pool, W, slot, ns, total_cols);
   if (tile_used) *tile_used = TC;
   // Pipeline depth: when every tile gets its own SM (one CTA per SM), a CTA has little work per
   // chunk and the copies' latency dominates -- deepen the ring up to ~200 KB of shared memory;
@@ -126,6 +130,7 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
     J.B = jobs[j].B;
     J.OUT = jobs[j].OUT;
     J.Dinv = (const TM*)jobs[j].Dinv;
+    J.dinv_cstride = jobs[j].dinv_cstride;
     J.ddiag = jobs[j].ddiag;
     J.norm = jobs[j].norm;
     tiles += (jobs[j].ncols + TC - 1) / TC;

@@ -6,6 +6,9 @@ steps, alpha = 0.5, gamma = (2 - alpha)/alpha = 3, H-matrix leaf 64 with recompr
 residual drops by 1e-8.  One step = one complete solve: every hot-path kernel (smoother
 half-sweeps, defect + restriction, prolongation, coarsest solve, defect norms) runs inside it.
 Also measured (key "workload_2d"): the 2D workload N = 511^2, M = 1024, alpha = 0.4, gamma = 2.5.
+Coarse-grid correction: the 255-point level (1D) / 31^2 level (2D) is solved exactly in FP64 (sine
+transform in space, one H-matrix triangular walk per spatial mode); --coarse-direct 1 runs the
+paper's recursion to one point instead.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-2d]
 
@@ -55,13 +58,28 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--coarse-direct", type=int, default=-1,
+                    help="grid size solved exactly as coarse-grid correction (-1: 255 in 1D, 31 in 2D; "
+                         "1: the paper's recursion to one point)")
     return ap.parse_args()
+
+
+def coarse_direct(a, dim, N):
+    """Coarse level solved exactly (FP64 sine transform + one H-matrix walk per mode)."""
+    n = a.coarse_direct if a.coarse_direct >= 0 else (255 if dim == 1 else 31)
+    return n if 1 < n < N else 1
+
+
+def coarse_desc(n):
+    return ("recursion to one point (the paper's cycle)" if n <= 1 else
+            f"exact FP64 solve on the {n}-point level (DST-I in space, one H-matrix walk per mode)")
 
 
 def workload(a):
     gamma = (2 - a.alpha) / a.alpha
     return {"workload": f"1D H-matrix, N={a.N}, M={a.M}, alpha={a.alpha}, gamma={gamma:.4g}, leaf 64, tol 1e-10, "
                         f"V(1,1) to relres {a.rtol:g}",
+            "coarse_solve": coarse_desc(coarse_direct(a, 1, a.N)),
             "dim": 1, "N": a.N, "M": a.M, "alpha": a.alpha, "gamma": gamma, "leaf": 64, "tol": 1e-10,
             "cycle": "V(1,1)", "rtol": a.rtol, "source": "manufactured t^alpha sin(pi x)",
             "l2": "inputs larger than L2 (u, f 134 MB each)"}
@@ -195,7 +213,7 @@ def timed_solves(P, f, steps, warmup, rtol, stream, dist):
     return {"ms": ms, "cycles": cycles, "relres": rr, "cnt": cnt, "u": u}
 
 
-def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, dist, dev):
+def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, dist, dev, nc=1):
     import torch
     t0 = time.perf_counter()
     H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
@@ -206,6 +224,7 @@ def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, di
     res = {}
     for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
         P = fh.Problem(H, dim, N, 1.0, prec, stream)
+        P.set_coarse_direct(nc)
         r = timed_solves(P, f, steps, warmup, rtol, stream, dist)
         r["P"] = P
         r["time_to_rtol_s"] = r["ms"] / steps / 1e3
@@ -225,7 +244,7 @@ def time_once(fn, stream):
     return e0.elapsed_time(e1) / 1e3, out
 
 
-def measure_warmstart(fh, stream, dev, rtol):
+def measure_warmstart(fh, stream, dev, rtol, nc=1):
     """2D N=1023^2, M=512, gamma=2, GRF source (ell = 0.1): FP64 zero guess, mixed zero guess, and
     mixed from the learned warm start (network trained on library solves at N=255^2, same M)."""
     import torch
@@ -242,11 +261,13 @@ def measure_warmstart(fh, stream, dev, rtol):
     f = warmstart.source_field(dim, 999, t[1:], N)
     out = {"workload": f"2D N={N}^2, M={M}, alpha={alpha}, gamma={gamma}, GRF source (length scale 0.1), "
                        f"relres {rtol:g} of max|F| (same absolute target for every start)",
+           "coarse_solve": coarse_desc(nc),
            "training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train, "loss": losses[-1],
                         "params": net.num_params(), "train_grid": "N=255^2, M=512, 8 alphas"}}
     for name, prec, warm in (("fp64_zero", fh.FP64, False), ("mixed_zero", fh.MIXED_FP32, False),
                              ("mixed_warm", fh.MIXED_FP32, True)):
         P = fh.Problem(H, dim, N, 1.0, prec, stream)
+        P.set_coarse_direct(nc)
         P.set_rtol_reference(1)
         u = torch.zeros_like(f)
         if warm:  # untimed warm-up of the prediction and the solve
@@ -358,7 +379,8 @@ def main():
     dof = a.N * a.M
 
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    H, f, res, t_hbuild = measure(fh, inputs, 1, a.N, a.M, a.alpha, gamma, a.steps, a.warmup, a.rtol, stream, dist, dev)
+    H, f, res, t_hbuild = measure(fh, inputs, 1, a.N, a.M, a.alpha, gamma, a.steps, a.warmup, a.rtol, stream, dist, dev,
+                                  coarse_direct(a, 1, a.N))
     clk = clocks.stop() if clocks else None
 
     k_ref = res["fp64"]["cycles"] / a.steps
@@ -393,13 +415,14 @@ def main():
         torch.cuda.empty_cache()
         N2, M2, al2, ga2 = 511, 1024, 0.4, 2.5
         st2, wu2 = min(a.steps, 2), 1
-        H2, f2, res2, tb2 = measure(fh, inputs, 2, N2, M2, al2, ga2, st2, wu2, a.rtol, stream, dist, dev)
+        nc2 = coarse_direct(a, 2, N2)
+        H2, f2, res2, tb2 = measure(fh, inputs, 2, N2, M2, al2, ga2, st2, wu2, a.rtol, stream, dist, dev, nc2)
         k2 = res2["fp64"]["cycles"] / st2
         dof2 = N2 * N2 * M2
         for r in res2.values():
             r["value"] = dof2 * k2 * ws / r["time_to_rtol_s"]
         w2d = {"workload": f"2D H-matrix, N={N2}^2, M={M2}, alpha={al2}, gamma={ga2}, leaf 64, tol 1e-10, V(1,1) to "
-                           f"relres {a.rtol:g}",
+                           f"relres {a.rtol:g}", "coarse_solve": coarse_desc(nc2),
                "fp64": summary(res2["fp64"], st2), "mixed": summary(res2["mixed"], st2),
                "speedup_mixed_vs_fp64": res2["fp64"]["time_to_rtol_s"] / res2["mixed"]["time_to_rtol_s"],
                "roofline_fp64": roofline(H2, res2["fp64"], N2 * N2 / 2.0, "fp64"),
@@ -410,7 +433,7 @@ def main():
     bat = None
     if not a.no_2d:
         torch.cuda.empty_cache()
-        wws = measure_warmstart(fh, stream, dev, a.rtol)
+        wws = measure_warmstart(fh, stream, dev, a.rtol, coarse_direct(a, 2, 1023))
         torch.cuda.empty_cache()
         bat = measure_batched(fh, inputs, stream, dev, a.rtol)
         torch.cuda.empty_cache()

@@ -95,12 +95,18 @@ int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles);
  * 2 FP32 throughout.  The outer defect and the update of u are FP64 in every mode. */
 int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode);
 /* Resets the counters below and, if enable != 0, records CUDA events on the problem's stream
- * around every smoother launch on the finest grid (the dominant kernel). */
+ * around every smoother launch on the finest grid and every FP64 defect product on the finest
+ * grid (the stopping test's and the mixed path's outer defects). */
 int fhmg_problem_profile(fhmg_problem p, int enable);
 /* Synchronises the stream and reports, since the last fhmg_problem_profile: the number of
  * kernel launches issued, the number of finest-grid smoother launches timed and their summed
  * device time in milliseconds.  Any pointer may be NULL. */
 int fhmg_problem_counters(fhmg_problem p, long long* launches, long long* smooth_launches, double* smooth_ms);
+/* Synchronises the stream and reports, since the last fhmg_problem_profile: the number of
+ * finest-grid FP64 defect products timed, their summed device time in milliseconds, and the
+ * finest grid's point count (a full defect walks that many columns; the stopping test of the
+ * FP64 path walks the first colour only).  Any pointer may be NULL. */
+int fhmg_problem_defect_timing(fhmg_problem p, long long* defect_launches, double* defect_ms, long long* columns);
 
 /* --- the hot-path steps, exposed one by one (each is one or more kernel launches) --- */
 
@@ -110,6 +116,13 @@ int fhmg_problem_counters(fhmg_problem p, long long* launches, long long* smooth
 int fhmg_line_solve(fhmg_problem p, int level, double* X, const double* B, long long ncols);
 /* Algorithm 3 over many columns: Y = R~ X; device [M][ncols]; Y must not alias X. */
 int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols);
+/* The same two steps with the mixed path's FP32 products (mixed-precision problems only; EINVAL
+ * otherwise): H-matrix entries and x tiles in FP32, accumulation in FP32 per leaf, the diagonal
+ * of the diagonal leaves (and of the level inverses) applied in FP64, FP64 arrays in and out.
+ * tile: 0 automatic, else the column tile (1, 2, 4, ..., 32); with leaf 64 and tensor cores
+ * enabled (fhmg_problem_set_tensor_cores) tiles 16 and 32 run on the tensor cores. */
+int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, long long ncols, int tile);
+int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols, int tile);
 /* nsweeps red-black zebra-in-time sweeps (Section 4) on the finest grid: u updated in place,
  * F the full right-hand side (f + d_{m,m} g). */
 int fhmg_smooth(fhmg_problem p, double* u, const double* F, int nsweeps);
@@ -160,6 +173,12 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
  * 1 ||r_k|| <= rtol max|F| -- the same absolute target whatever the initial guess, used to compare
  * a warm start with the zero initial guess fairly. */
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
+
+/* FP32 products of the mixed path on the tensor cores (enable != 0, the default): with leaf 64,
+ * walks with column tiles of 16 or 32 run as mma.sync m16n8k8 TF32 products split in three
+ * (hi*hi + hi*lo + lo*hi, hi = tf32(a), lo = tf32(a - hi): FP32 accuracy, FP32 accumulation);
+ * enable = 0 keeps every walk on the FP32 SIMT kernel.  Clears the autotuned tiles. */
+int fhmg_problem_set_tensor_cores(fhmg_problem p, int enable);
 
 /* Coarse-grid solver of fhmg_vcycle / fhmg_solve.  n <= 1 (default): the paper's recursion to one
  * interior point (Algorithm 2; the one-point system is solved by the line solve).  n = 2^k - 1 < N:

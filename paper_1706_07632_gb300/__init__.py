@@ -43,8 +43,11 @@ _SIGS = {
     "fhmg_problem_set_inner": (_I, [_P, _I]),
     "fhmg_problem_set_mixed_storage": (_I, [_P, _I]),
     "fhmg_problem_counters": (_I, [_P, _c.POINTER(_LL), _c.POINTER(_LL), _c.POINTER(_D)]),
+    "fhmg_problem_defect_timing": (_I, [_P, _c.POINTER(_LL), _c.POINTER(_D), _c.POINTER(_LL)]),
     "fhmg_line_solve": (_I, [_P, _I, _P, _P, _LL]),
     "fhmg_hmatvec": (_I, [_P, _P, _P, _LL]),
+    "fhmg_line_solve_f32": (_I, [_P, _I, _P, _P, _LL, _I]),
+    "fhmg_hmatvec_f32": (_I, [_P, _P, _P, _LL, _I]),
     "fhmg_smooth": (_I, [_P, _P, _P, _I]),
     "fhmg_residual": (_I, [_P, _P, _P, _P, _P]),
     "fhmg_restrict_residual": (_I, [_P, _P, _P, _P]),
@@ -59,6 +62,7 @@ _SIGS = {
     "fhmg_autotune_leaf": (_I, [_D, _D, _D, _I, _D, _I, _I, _D, _I, _P, _c.POINTER(_I), _c.POINTER(_D)]),
     "fhmg_problem_set_rtol_reference": (_I, [_P, _I]),
     "fhmg_problem_set_coarse_direct": (_I, [_P, _I]),
+    "fhmg_problem_set_tensor_cores": (_I, [_P, _I]),
     "fhmg_wsnet_create": (_I, [_I, _I, _c.c_ulonglong, _c.POINTER(_P)]),
     "fhmg_wsnet_destroy": (_I, [_P]),
     "fhmg_wsnet_num_params": (_I, [_P, _c.POINTER(_LL)]),
@@ -189,6 +193,10 @@ class Problem:
         (n <= 1: recursion to one point, the paper's cycle)."""
         _check(lib().fhmg_problem_set_coarse_direct(self._p, n))
 
+    def set_tensor_cores(self, enable=True):
+        """FP32 products on the tensor cores (3xTF32 mma.sync) where the column tile allows."""
+        _check(lib().fhmg_problem_set_tensor_cores(self._p, 1 if enable else 0))
+
     def set_mixed_storage(self, mode):
         """0 automatic, 1 FP64 storage with FP32 products, 2 FP32 throughout (inner cycles)."""
         _check(lib().fhmg_problem_set_mixed_storage(self._p, mode))
@@ -201,12 +209,24 @@ class Problem:
         _check(lib().fhmg_problem_counters(self._p, ctypes.byref(n), ctypes.byref(ns), ctypes.byref(ms)))
         return {"launches": n.value, "smooth_launches": ns.value, "smooth_ms": ms.value}
 
+    def defect_timing(self):
+        n, ms, cols = _LL(), _D(), _LL()
+        _check(lib().fhmg_problem_defect_timing(self._p, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(cols)))
+        return {"defect_launches": n.value, "defect_ms": ms.value, "columns": cols.value}
+
     def line_solve(self, level, X, B):
         ncols = B.numel() // self.M
         _check(lib().fhmg_line_solve(self._p, level, _ptr(X), _ptr(B), ncols))
 
     def hmatvec(self, Y, X):
         _check(lib().fhmg_hmatvec(self._p, _ptr(Y), _ptr(X), X.numel() // self.M))
+
+    def line_solve_f32(self, level, X, B, tile=0):
+        """fhmg_line_solve with the mixed path's FP32 products (tile 16/32: tensor cores)."""
+        _check(lib().fhmg_line_solve_f32(self._p, level, _ptr(X), _ptr(B), B.numel() // self.M, tile))
+
+    def hmatvec_f32(self, Y, X, tile=0):
+        _check(lib().fhmg_hmatvec_f32(self._p, _ptr(Y), _ptr(X), X.numel() // self.M, tile))
 
     def smooth(self, u, F, nsweeps=1):
         _check(lib().fhmg_smooth(self._p, _ptr(u), _ptr(F), nsweeps))

@@ -71,6 +71,7 @@ struct LevelData {
   float* RC32 = nullptr;
   double* Dinv64 = nullptr;    // (D_ii + s I)^{-1}, FP64, in the chunk layout (to_panel_layout)
   float* Dinv32 = nullptr;     // the same in FP32 without its diagonal (mixed path)
+  float* Dinv32m = nullptr;    // ... and as TF32 hi/lo pairs in the tensor-core layout (to_mma_layout)
   double* dinvdiag = nullptr;  // the inverses' diagonal, FP64 (mixed path) ...
   float* dinvdiag32 = nullptr; // ... and FP32 (FP32 inner cycles)
 };
@@ -85,6 +86,8 @@ struct fhmg_problem_s {
   int M = 0, L = 0, nb = 0;
   DevPanel panel64;  // chunk stream, FP64 matrices
   DevPanel panel32;  // chunk stream, FP32 matrices (mixed path)
+  DevPanel panel32m; // the same in the tensor-core layout (build_panel_mma)
+  int use_mma = 1;   // FP32 products on the tensor cores where the column tile allows
   double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path) ...
   float* rdiag32 = nullptr; // ... and its FP32 copy (FP32 inner cycles)
   std::vector<LevelData> lev;
@@ -118,6 +121,8 @@ struct fhmg_problem_s {
   bool profile = false;         // record events around finest-level smoother walks
   std::vector<cudaEvent_t> ev;  // start/stop pairs
   size_t ev_used = 0;
+  std::vector<cudaEvent_t> evd; // start/stop pairs around finest-grid FP64 defect products
+  size_t evd_used = 0;
 };
 
 namespace {
@@ -142,10 +147,14 @@ int upload(std::vector<void*>& list, const std::vector<S>& src, const T** out, s
   return FHMG_OK;
 }
 
-// Uploads the chunk stream of the H-matrix (elem_bytes 8: FP64 products, 4: FP32 products).
+// Uploads the chunk stream of the H-matrix (elem_bytes 8: FP64 products, 4: FP32 products,
+// 0: FP32 products in the tensor-core layout).
 int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, DevPanel& D) {
   fhmg::PanelHost ph;
-  fhmg::build_panel(h, f, elem_bytes, ph);
+  if (elem_bytes == 0)
+    fhmg::build_panel_mma(h, f, ph);
+  else
+    fhmg::build_panel(h, f, elem_bytes, ph);
   const unsigned char* pkg;
   const int* chunks;
   const int* cptr;
@@ -161,6 +170,7 @@ int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, Dev
   D.d.W = ph.W;
   D.d.slot_bytes = ph.slot_bytes;
   D.d.ns = 2;
+  D.d.far = ph.far ? 1 : 0;
   return FHMG_OK;
 }
 
@@ -174,14 +184,23 @@ int check_dims(fhmg_problem p) {
   return FHMG_OK;
 }
 
-int record_event(fhmg_problem p) {
-  if (p->ev_used == p->ev.size()) {
+int record_event(fhmg_problem p, std::vector<cudaEvent_t>& ev, size_t& used) {
+  if (used == ev.size()) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
-    p->ev.push_back(e);
+    ev.push_back(e);
   }
-  CK(cudaEventRecord(p->ev[p->ev_used++], p->st));
+  CK(cudaEventRecord(ev[used++], p->st));
   return FHMG_OK;
+}
+
+double pair_ms(const std::vector<cudaEvent_t>& ev, size_t used) {
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < used; i += 2) {
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, ev[i], ev[i + 1]) == cudaSuccess) ms += x;
+  }
+  return ms;
 }
 
 int walk_status(int s, const std::string& err) {
@@ -216,6 +235,10 @@ fhmg::WalkArgsT<T> smooth_job(fhmg_problem p, int l, int kind, const Geo& g, lon
   LevelData& lv = p->lev[l];
   fhmg::WalkArgsT<T> a{};
   a.P = kind == K64 ? p->panel64.d : p->panel32.d;
+  if (kind != K64 && p->use_mma && p->panel32m.d.pkg) {
+    a.PM = p->panel32m.d;
+    a.DinvM = lv.Dinv32m;
+  }
   a.mode = fhmg::MODE_SMOOTH;
   a.geo = g;
   a.ncols = nc;
@@ -237,6 +260,7 @@ fhmg::WalkArgsT<T> matvec_job(fhmg_problem p, int kind, long long nc, const T* X
                               unsigned long long* norm) {
   fhmg::WalkArgsT<T> a{};
   a.P = kind == K64 ? p->panel64.d : p->panel32.d;
+  if (kind != K64 && p->use_mma && p->panel32m.d.pkg) a.PM = p->panel32m.d;
   a.mode = fhmg::MODE_MATVEC;
   a.geo = Geo{0, 0, 0, nc, 0.0};
   a.ncols = nc;
@@ -306,9 +330,9 @@ int sweep(fhmg_problem p, int l, T* u, const T* F, int kind) {
     if (nc == 0) continue;
     Geo g{p->dim, lv.N, colour, lv.npts, lv.inv_h2};
     const bool rec = p->profile && l == p->nlev - 1;
-    if (rec) TRY(record_event(p));
+    if (rec) TRY(record_event(p, p->ev, p->ev_used));
     TRY(walk_smooth<T>(p, l, kind, g, nc, u, F));
-    if (rec) TRY(record_event(p));
+    if (rec) TRY(record_event(p, p->ev, p->ev_used));
   }
   return FHMG_OK;
 }
@@ -419,14 +443,18 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
                                                                                   p->Xs, p->Rs);
     ++p->launches;
     CK(cudaGetLastError());
+    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
     TRY(walk_matvec<double>(p, K64, nc, p->Xs, p->Rs, nullptr, p->dnorm));
+    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
   } else {
     double* dst = R ? R : p->Rs;
     fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
                                                                                        u, F, nullptr, dst);
     ++p->launches;
     CK(cudaGetLastError());
+    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
     TRY(walk_matvec<double>(p, K64, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
+    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
   }
   return read_norm(p, out);
 }
@@ -831,10 +859,12 @@ int fhmg_hmatrix_destroy(fhmg_hmatrix h) {
 int fhmg_problem_destroy(fhmg_problem p) {
   if (!p) return FHMG_OK;
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->evd) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
   for (void* a : p->dallocs) cudaFree(a);
   for (void* a : p->panel64.allocs) cudaFree(a);
   for (void* a : p->panel32.allocs) cudaFree(a);
+  for (void* a : p->panel32m.allocs) cudaFree(a);
   delete p;
   return FHMG_OK;
 }
@@ -869,6 +899,7 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   if ((st = upload_panel(h->host, h->flat, 8, p->panel64)) != FHMG_OK) return bail(st);
   if (mixed) {
     if ((st = upload_panel(h->host, h->flat, 4, p->panel32)) != FHMG_OK) return bail(st);
+    if (p->L == 64 && (st = upload_panel(h->host, h->flat, 0, p->panel32m)) != FHMG_OK) return bail(st);
     std::vector<double> rd((size_t)p->nb * p->L);
     for (int i = 0; i < p->nb; ++i)
       for (int r = 0; r < p->L; ++r) rd[(size_t)i * p->L + r] = h->host.dense[h->host.diag[i]].D[(size_t)r * p->L + r];
@@ -909,6 +940,13 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
       const float* dd32;
       if ((st = upload(p->allocs, dg, &dd32, nullptr)) != FHMG_OK) return bail(st);
       lv.dinvdiag32 = const_cast<float*>(dd32);
+      if (p->L == 64) {
+        std::vector<float> m(inv.size() * 2);
+        for (int i = 0; i < p->nb; ++i) fhmg::to_mma_layout(&inv[i * LL], p->L, true, &m[i * LL * 2]);
+        const float* dm;
+        if ((st = upload(p->allocs, m, &dm, nullptr)) != FHMG_OK) return bail(st);
+        lv.Dinv32m = const_cast<float*>(dm);
+      }
     }
     if (l < nlev - 1) {
       if ((st = dalloc(p->allocs, &lv.E, (size_t)lv.npts * M)) != FHMG_OK) return bail(st);
@@ -1078,6 +1116,13 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   return FHMG_OK;
 }
 
+int fhmg_problem_set_tensor_cores(fhmg_problem p, int enable) {
+  TRY(check_dims(p));
+  p->use_mma = enable != 0;
+  p->tune.clear();  // tuned tiles were timed with the other kernels
+  return FHMG_OK;
+}
+
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref) {
   TRY(check_dims(p));
   if (ref != 0 && ref != 1) return fail(FHMG_EINVAL, "reference must be 0 (initial defect) or 1 (max |F|)");
@@ -1090,6 +1135,7 @@ int fhmg_problem_profile(fhmg_problem p, int enable) {
   CK(cudaStreamSynchronize(p->st));
   p->profile = enable != 0;
   p->ev_used = 0;
+  p->evd_used = 0;
   p->launches = 0;
   return FHMG_OK;
 }
@@ -1097,15 +1143,18 @@ int fhmg_problem_profile(fhmg_problem p, int enable) {
 int fhmg_problem_counters(fhmg_problem p, long long* launches, long long* smooth_launches, double* smooth_ms) {
   TRY(check_dims(p));
   CK(cudaStreamSynchronize(p->st));
-  double ms = 0.0;
-  for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
-    float x = 0.f;
-    CK(cudaEventElapsedTime(&x, p->ev[i], p->ev[i + 1]));
-    ms += x;
-  }
   if (launches) *launches = p->launches;
   if (smooth_launches) *smooth_launches = (long long)(p->ev_used / 2);
-  if (smooth_ms) *smooth_ms = ms;
+  if (smooth_ms) *smooth_ms = pair_ms(p->ev, p->ev_used);
+  return FHMG_OK;
+}
+
+int fhmg_problem_defect_timing(fhmg_problem p, long long* defect_launches, double* defect_ms, long long* columns) {
+  TRY(check_dims(p));
+  CK(cudaStreamSynchronize(p->st));
+  if (defect_launches) *defect_launches = (long long)(p->evd_used / 2);
+  if (defect_ms) *defect_ms = pair_ms(p->evd, p->evd_used);
+  if (columns) *columns = p->lev[p->nlev - 1].npts;
   return FHMG_OK;
 }
 
@@ -1122,6 +1171,33 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
   if (!X || !Y || ncols < 0 || X == Y) return fail(FHMG_EINVAL, "bad arrays");
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
   TRY(walk_matvec<double>(p, K64, ncols, X, Y, Y, nullptr));
+  scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
+  ++p->launches;
+  CK(cudaGetLastError());
+  return FHMG_OK;
+}
+
+int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, long long ncols, int tile) {
+  TRY(check_dims(p));
+  if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
+  if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
+  if (!X || !B || ncols < 0 || tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
+    return fail(FHMG_EINVAL, "bad arguments");
+  Geo g{0, 0, 0, ncols, 0.0};
+  std::vector<fhmg::WalkArgsT<double>> j{smooth_job<double>(p, level, KSPLIT, g, ncols, X, B)};
+  j[0].tile = tile;
+  return launch_jobs(p->st, KSPLIT, j, &p->launches);
+}
+
+int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols, int tile) {
+  TRY(check_dims(p));
+  if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
+  if (!X || !Y || ncols < 0 || X == Y || tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
+    return fail(FHMG_EINVAL, "bad arguments");
+  CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
+  std::vector<fhmg::WalkArgsT<double>> j{matvec_job<double>(p, KSPLIT, ncols, X, Y, Y, nullptr)};
+  j[0].tile = tile;
+  TRY(launch_jobs(p->st, KSPLIT, j, &p->launches));
   scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
   ++p->launches;
   CK(cudaGetLastError());

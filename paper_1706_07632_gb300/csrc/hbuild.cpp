@@ -6,6 +6,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <numeric>
 
@@ -561,6 +562,109 @@ void build_panel(const HostH& h, const FlatH& f, int eb, PanelHost& out) {
     out.chunks[out.chunks.size() - 4] |= 1 << 12;  // the leaf row's last chunk
     out.cptr[i + 1] = (int)(out.chunks.size() / 4);
   }
+}
+
+namespace {
+
+// round to the nearest TF32 value (10 explicit mantissa bits), ties away from zero
+float tf32_round(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7f800000u) != 0x7f800000u) b = (b + 0x1000u) & 0xffffe000u;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
+// float index of part hl of entry (r, k) in the fragment layout of an R x K chunk matrix
+size_t mma_index(int r, int k, int nkb, int hl) {
+  const int rt = r / 16, half = (r % 16) / 8, g = r % 8;
+  const int kb = k / 16, t = (k % 16) / 4, e = k % 4;
+  const int lane = g * 4 + t;
+  return (((((size_t)rt * nkb + kb) * 2 + hl) * 2 + half) * 32 + lane) * 4 + e;
+}
+
+void put_mma(std::vector<unsigned char>& pkg, size_t off, int r, int k, int nkb, double v) {
+  const float hi = tf32_round((float)v);
+  const float lo = tf32_round((float)(v - (double)hi));
+  std::memcpy(&pkg[off + mma_index(r, k, nkb, 0) * 4], &hi, 4);
+  std::memcpy(&pkg[off + mma_index(r, k, nkb, 1) * 4], &lo, 4);
+}
+
+}  // namespace
+
+void build_panel_mma(const HostH& h, const FlatH& f, PanelHost& out) {
+  const int L = f.L, nb = f.nb;
+  const int nkbL = (L + 15) / 16;
+  out = PanelHost();
+  out.cptr.assign(nb + 1, 0);
+  int maxdist = 0;
+  for (int i = 0; i < nb; ++i)
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) maxdist = std::max(maxdist, i - f.dlist_col[d]);
+  out.W = std::min(8, maxdist + 1);
+  out.far = maxdist + 1 > out.W;
+  auto add_chunk = [&](int type, int count, int aux, size_t bytes) -> size_t {
+    size_t off = out.pkg.size();
+    size_t nbytes = pad16(bytes);
+    out.pkg.resize(off + nbytes, 0);
+    out.chunks.push_back(type | (count << 4));
+    out.chunks.push_back(aux);
+    out.chunks.push_back((int)nbytes);
+    out.chunks.push_back((int)(off / 16));
+    out.slot_bytes = std::max(out.slot_bytes, (int)nbytes);
+    return off;
+  };
+  const size_t sq = (size_t)nkbL * 16 * nkbL * 16 * 2 * 4;  // padded L x L, hi + lo
+  auto put_square = [&](const double* D, size_t off, bool zero_diag) {
+    for (int r = 0; r < L; ++r)
+      for (int k = 0; k < L; ++k) put_mma(out.pkg, off, r, k, nkbL, (zero_diag && k == r) ? 0.0 : D[(size_t)r * L + k]);
+  };
+  for (int i = 0; i < nb; ++i) {
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) {
+      size_t off = add_chunk(CH_DENSE, L, f.dlist_col[d], sq);
+      put_square(&f.dense_data[(size_t)f.dlist_blk[d] * L * L], off, false);
+    }
+    const int K = f.uptr[i + 1] - f.uptr[i];
+    for (int k0 = 0; k0 < K; k0 += L) {
+      const int kc = std::min(L, K - k0);
+      const int kp = (kc + 15) / 16 * 16;
+      const size_t mat = (size_t)nkbL * 16 * kp * 2 * 4;
+      size_t off = add_chunk(CH_UPART, kp, k0, mat + (size_t)kp * 4);
+      for (int r = 0; r < L; ++r)
+        for (int kk = 0; kk < kc; ++kk) put_mma(out.pkg, off, r, kk, kp / 16, f.udata[f.uoff[i] + (size_t)r * K + k0 + kk]);
+      for (int kk = 0; kk < kp; ++kk) {
+        int z = f.uz[f.uptr[i] + k0 + (kk < kc ? kk : 0)];
+        std::memcpy(&out.pkg[off + mat + (size_t)kk * 4], &z, 4);
+      }
+    }
+    {
+      size_t off = add_chunk(CH_DIAG, L, i, sq);
+      put_square(&f.dense_data[(size_t)f.diag_blk[i] * L * L], off, true);
+    }
+    const int Kv = f.vptr[i + 1] - f.vptr[i];
+    for (int k0 = 0; k0 < Kv; k0 += L) {
+      const int kc = std::min(L, Kv - k0);
+      const int rp = (kc + 15) / 16 * 16;
+      const size_t mat = (size_t)rp * nkbL * 16 * 2 * 4;
+      size_t off = add_chunk(CH_VPART, kc, k0, mat + (size_t)kc * 4);
+      for (int kk = 0; kk < kc; ++kk)
+        for (int c = 0; c < L; ++c) put_mma(out.pkg, off, kk, c, nkbL, f.vdata[f.voff[i] + (size_t)(k0 + kk) * L + c]);
+      for (int kk = 0; kk < kc; ++kk) {
+        int code = 2 * f.vz[f.vptr[i] + k0 + kk] + f.vinit[f.vptr[i] + k0 + kk];
+        std::memcpy(&out.pkg[off + mat + (size_t)kk * 4], &code, 4);
+      }
+    }
+    out.chunks[out.chunks.size() - 4] |= 1 << 12;
+    out.cptr[i + 1] = (int)(out.chunks.size() / 4);
+  }
+}
+
+void to_mma_layout(const double* A, int L, bool zero_diag, float* out) {
+  const int nkb = (L + 15) / 16;
+  std::vector<unsigned char> buf((size_t)nkb * 16 * nkb * 16 * 2 * 4, 0);
+  for (int r = 0; r < L; ++r)
+    for (int k = 0; k < L; ++k) put_mma(buf, 0, r, k, nkb, (zero_diag && k == r) ? 0.0 : A[(size_t)r * L + k]);
+  std::memcpy(out, buf.data(), buf.size());
 }
 
 void to_panel_layout(const double* A, int L, int eb, bool zero_diag, double* out) {

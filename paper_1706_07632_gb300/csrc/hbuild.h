@@ -92,10 +92,25 @@ struct PanelHost {
   std::vector<int> cptr;     // nb+1 chunk ranges per leaf row
   int slot_bytes = 0;        // largest chunk
   int W = 1;                 // depth of the ring of x tiles (max near-field distance + 1, <= 8)
+  bool far = false;          // some near-field block lies further back than the ring reaches
 };
 
 // elem_bytes = 8 (FP64 matrices) or 4 (FP32 matrices)
 void build_panel(const HostH& h, const FlatH& f, int elem_bytes, PanelHost& out);
+
+// The same stream for the tensor-core walk (FP32 products as three TF32 products, hi*hi + hi*lo +
+// lo*hi): every chunk matrix (R rows, K reduction index) is padded with zeros to multiples of 16
+// and stored as TF32 pairs hi = tf32(a), lo = tf32(a - hi) in the order in which the mma.sync
+// m16n8k8 A operand is loaded, one 16-byte vector per lane: float index
+//   ((((rt * NKB + kb) * 2 + hl) * 2 + half) * 32 + lane) * 4 + e
+// holds part hl (0 hi, 1 lo) of entry (rt*16 + half*8 + lane/4, kb*16 + 4*(lane%4) + e), NKB = K/16.
+// A warp's load of one (rt, kb, hl, half) is 512 contiguous bytes.  DENSE and DIAG: R = K = L;
+// UPART: R = L, K = count padded to 16 (z indices padded with the slab's first); VPART: R = count
+// padded to 16, K = L.  The DIAG blocks carry no diagonal (applied in the grid precision).
+void build_panel_mma(const HostH& h, const FlatH& f, PanelHost& out);
+// The row-major L x L matrix A in that layout (hi/lo pairs, L*L*2 floats for L a multiple of 16).
+void to_mma_layout(const double* A, int L, bool zero_diag, float* out);
+
 
 // Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
 // Returns 0 on success, < 0 on invalid arguments.

@@ -44,6 +44,7 @@ struct PanelDev {
   const int4* chunks;        // type | count << 4 | last << 12, aux, bytes, offset / 16
   const int* cptr;           // nb + 1
   int nb, L, pool, W, slot_bytes, ns;
+  int far;                   // 1: some near-field block lies beyond the ring of W leaf tiles
 };
 
 // 16-byte vectors of the chunk layout
@@ -382,7 +383,8 @@ __global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant_
     }
     double local_max = 0.0;
     // right-hand side, x tile (product) and diagonal term (FP32 products) of the next leaf,
-    // prefetched a leaf ahead by the threads that use them
+    // prefetched a leaf ahead by the threads that use them (issued at the diagonal step: issuing
+    // them a whole leaf ahead raised the register count past the two-CTA occupancy)
     T bn[Q], xn[Q], dn[Q];
     auto load_rhs = [&](int leaf) {
 #pragma unroll
@@ -501,7 +503,7 @@ __global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant_
               }
             }
           }
-          load_rhs(i + 1);  // the next leaf's loads overlap the V slabs and the next chunk waits
+          load_rhs(i + 1);  // the next leaf's loads overlap the V slabs and the next chunks
           // smoother: x_i is published for the V slabs (the product wrote its x_i before the first
           // barrier; a warp can rewrite an operand only after every warp reached the next one)
           if (MODE == MODE_SMOOTH && !consumer_sync()) return;

@@ -23,6 +23,8 @@ struct WalkArgsT {
   unsigned long long* norm;
   int* err;                    // device error word (bounded-wait timeout); the first job's is used
   int tile;                    // 0: automatic, else the column tile TC (the first job's is used)
+  PanelDev PM;                 // FP32 products only: the stream in the tensor-core layout (pkg NULL: none)
+  const void* DinvM;           // and the level inverses in that layout
 };
 using WalkArgs = WalkArgsT<double>;
 
@@ -31,5 +33,19 @@ using WalkArgs = WalkArgsT<double>;
 int walk_launch_dd(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 int walk_launch_df(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 int walk_launch_ff(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std::string* err, int* tile_used);
+
+// Tensor-core walks (FP32 products, leaf 64, TC 16 or 32), walk_mma.cu.  B.ns is chosen here.
+int mma_launch_df(cudaStream_t st, WalkBatch<double, float>& B, int TC, int mode, std::string* err);
+int mma_launch_ff(cudaStream_t st, WalkBatch<float, float>& B, int TC, int mode, std::string* err);
+template <typename T>
+inline int mma_launch(cudaStream_t st, WalkBatch<T, float>& B, int TC, int mode, std::string* err);
+template <>
+inline int mma_launch<double>(cudaStream_t st, WalkBatch<double, float>& B, int TC, int mode, std::string* err) {
+  return mma_launch_df(st, B, TC, mode, err);
+}
+template <>
+inline int mma_launch<float>(cudaStream_t st, WalkBatch<float, float>& B, int TC, int mode, std::string* err) {
+  return mma_launch_ff(st, B, TC, mode, err);
+}
 
 }  // namespace fhmg

@@ -93,6 +93,48 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
   int ns = panel_slots(slot);
   long long total_cols = 0;
   for (int j = 0; j < njobs; ++j) total_cols += jobs[j].ncols;
+  if constexpr (sizeof(TM) == 4) {
+    // FP32 products on the tensor cores: leaf 64, tile 16 or 32 (tile 16 once the columns fill
+    // about half the SMs with 16 each, 32 once they fill every SM with 32)
+    bool mma_ok = L == 64;
+    for (int j = 0; j < njobs; ++j)
+      mma_ok = mma_ok && jobs[j].PM.pkg != nullptr && !jobs[j].PM.far && jobs[j].dinv_cstride == 0;
+    if (mma_ok) {
+      int tcm = jobs[0].tile;
+      if (tcm == 0) tcm = total_cols >= 32LL * kPanelSMs ? 32 : total_cols >= 1024 ? 16 : 0;
+      if (tcm == 16 || tcm == 32) {
+        if (tile_used) *tile_used = tcm;
+        WalkBatch<T, float> Bm;
+        Bm.njobs = njobs;
+        Bm.pool = 0;
+        Bm.W = 1;
+        Bm.slot_bytes = 16;
+        Bm.err = jobs[0].err;
+        long long tiles = 0;
+        for (int j = 0; j < njobs; ++j) {
+          Bm.pool = std::max(Bm.pool, jobs[j].PM.pool);
+          Bm.W = std::max(Bm.W, jobs[j].PM.W);
+          Bm.slot_bytes = std::max(Bm.slot_bytes, jobs[j].PM.slot_bytes);
+          WalkJob<T, float>& J = Bm.job[j];
+          J.P = jobs[j].PM;
+          J.geo = jobs[j].geo;
+          J.ncols = jobs[j].ncols;
+          J.tile0 = tiles;
+          J.X = jobs[j].X;
+          J.B = jobs[j].B;
+          J.OUT = jobs[j].OUT;
+          J.Dinv = (const float*)jobs[j].DinvM;
+          J.dinv_cstride = 0;
+          J.ddiag = jobs[j].ddiag;
+          J.norm = jobs[j].norm;
+          tiles += (jobs[j].ncols + tcm - 1) / tcm;
+        }
+        Bm.ntiles = tiles;
+        Bm.ns = 2;
+        return mma_launch<T>(st, Bm, tcm, MODE, err);
+      }
+    }
+  }
   bool per_column_inverse = false;
   for (int j = 0; j < njobs; ++j) per_column_inverse |= jobs[j].dinv_cstride != 0;
   const int TC = per_column_inverse ? 1

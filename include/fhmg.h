@@ -90,9 +90,11 @@ int fhmg_problem_autotune(fhmg_problem p);
 /* Mixed path: V-cycles run on the correction equation between two FP64 defect evaluations
  * (>= 1; 0 restores the default: 2 with FP32 storage, 4 with FP64 storage). */
 int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles);
-/* Mixed path, storage of the inner cycles: 0 automatic (FP32 when 6e-8 * 4 (N+1)^2 / pi^2 <= 0.05,
- * i.e. N <= 1023), 1 FP64 grid functions / stencil / diagonal with FP32 H-matrix products,
- * 2 FP32 throughout.  The outer defect and the update of u are FP64 in every mode. */
+/* Mixed path, storage of the inner cycles: 0 automatic, per level: FP32 on every level whose
+ * stencil conditioning allows it (6e-8 * 4 (N+1)^2 / pi^2 <= 0.05, i.e. N <= 1023), FP64 grid
+ * functions / stencil / diagonal with FP32 H-matrix products on the finer ones (a coarse-grid
+ * correction below them then runs in FP32 storage); 1 FP64 storage with FP32 products on every
+ * level; 2 FP32 throughout.  The outer defect and the update of u are FP64 in every mode. */
 int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode);
 /* Resets the counters below and, if enable != 0, records CUDA events on the problem's stream
  * around every smoother launch on the finest grid and every FP64 defect product on the finest

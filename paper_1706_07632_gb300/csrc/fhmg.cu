@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -97,7 +98,7 @@ struct fhmg_problem_s {
   float* Xs32 = nullptr; // FP32 inner cycles of the mixed path: scratch, defect, correction
   float* Rs32 = nullptr;
   float* Ef32 = nullptr;
-  int mixed_storage = 0; // 0 automatic, 1 FP64 storage + FP32 products, 2 FP32 storage
+  int mixed_storage = 0; // 0 automatic per level, 1 FP64 storage + FP32 products, 2 FP32 storage
   int rtol_ref = 0;      // stopping test relative to: 0 the initial defect, 1 max |F|
   std::map<std::pair<int, long long>, int> tune;  // autotuned column tiles: (kind*2+mode, ncols) -> TC
   double* Ff = nullptr;  // f + d g when g is given
@@ -401,18 +402,62 @@ int direct_level(fhmg_problem p, int l, T* E, const T* RC) {
   return FHMG_OK;
 }
 
+__global__ void to_float_kernel(const double* x, float* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void to_double_kernel(const float* x, double* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+__global__ void add_float_kernel(double* y, const float* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += (double)x[i];
+}
+
+// Storage of a coarse-grid correction on level l inside FP64-storage inner cycles (automatic
+// mixed storage only): FP32 where the stencil's conditioning allows it,
+// eps32 * cond(A_h) ~ 6e-8 * 4 (N+1)^2 / pi^2 <= 0.05 (N <= 1023 per dimension).
+bool level_fp32(fhmg_problem p, int l) {
+  if (p->mixed_storage != 0) return false;
+  const double n1 = p->lev[l].N + 1.0;
+  return 6e-8 * 4.0 * n1 * n1 / (M_PI * M_PI) <= 0.05;
+}
+
+template <typename T>
+int vcycle_rec(fhmg_problem p, int l, T* u, const T* F, int nu1, int nu2, int kind);
+
+// The coarse-grid correction of level l (restricted defect in RC of level l - 1, result in E of
+// level l - 1): exact solve, FP32-storage cycle, or the recursion in T.
+template <typename T>
+int coarse_correction(fhmg_problem p, int l, int nu1, int nu2, int kind) {
+  LevelData& lc = p->lev[l - 1];
+  const long long n = lc.npts * p->M;
+  if (l - 1 == p->lcd) return direct_level<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc));
+  if constexpr (std::is_same<T, double>::value) {
+    if (kind == KSPLIT && level_fp32(p, l - 1)) {
+      to_float_kernel<<<blocks_for(n), 256, 0, p->st>>>(lc.RC, lc.RC32, n);
+      ++p->launches;
+      CK(cudaGetLastError());
+      CK(cudaMemsetAsync(lc.E32, 0, sizeof(float) * n, p->st));
+      TRY(vcycle_rec<float>(p, l - 1, lc.E32, lc.RC32, nu1, nu2, K32));
+      to_double_kernel<<<blocks_for(n), 256, 0, p->st>>>(lc.E32, lc.E, n);
+      ++p->launches;
+      CK(cudaGetLastError());
+      return FHMG_OK;
+    }
+  }
+  CK(cudaMemsetAsync(lev_E<T>(lc), 0, sizeof(T) * n, p->st));
+  return vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind);
+}
+
 template <typename T>
 int vcycle_rec(fhmg_problem p, int l, T* u, const T* F, int nu1, int nu2, int kind) {
   if (l == 0) return sweep<T>(p, 0, u, F, kind);  // one interior point: the colour-0 solve is exact
   for (int s = 0; s < nu1; ++s) TRY(sweep<T>(p, l, u, F, kind));
   LevelData& lc = p->lev[l - 1];
   TRY(restrict_defect<T>(p, l, u, F, lev_RC<T>(lc), kind));
-  if (l - 1 == p->lcd) {
-    TRY(direct_level<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc)));
-  } else {
-    CK(cudaMemsetAsync(lev_E<T>(lc), 0, sizeof(T) * lc.npts * p->M, p->st));
-    TRY(vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind));
-  }
+  TRY(coarse_correction<T>(p, l, nu1, nu2, kind));
   TRY(prolong_add<T>(p, l, lev_E<T>(lc), u));
   for (int s = 0; s < nu2; ++s) TRY(sweep<T>(p, l, u, F, kind));
   return FHMG_OK;
@@ -510,14 +555,6 @@ int solve_fp64(fhmg_problem p, double* u, const double* F, int nu1, int nu2, dou
   return FHMG_OK;
 }
 
-__global__ void to_float_kernel(const double* x, float* y, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
-}
-__global__ void add_float_kernel(double* y, const float* x, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] += (double)x[i];
-}
 
 __global__ void absmax_kernel(const double* x, long long n, unsigned long long* out) {
   double m = 0.0;

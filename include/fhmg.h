@@ -125,6 +125,9 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols);
  * enabled (fhmg_problem_set_tensor_cores) tiles 16 and 32 run on the tensor cores. */
 int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, long long ncols, int tile);
 int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols, int tile);
+/* Y = R~ X with the double-float products of fhmg_problem_set_defect_arith (mixed-precision
+ * problems only; EINVAL otherwise); device [M][ncols] FP64; tile 0 (automatic), 4, 8 or 16. */
+int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols, int tile);
 /* nsweeps red-black zebra-in-time sweeps (Section 4) on the finest grid: u updated in place,
  * F the full right-hand side (f + d_{m,m} g). */
 int fhmg_smooth(fhmg_problem p, double* u, const double* F, int nsweeps);
@@ -175,6 +178,13 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
  * 1 ||r_k|| <= rtol max|F| -- the same absolute target whatever the initial guess, used to compare
  * a warm start with the zero initial guess fairly. */
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
+
+/* Arithmetic of the mixed path's outer defect products (the FP64 residual that judges
+ * convergence): 1 (default) double-float -- pairs of floats with error-free transformations on
+ * the FP32 pipe (entries and x split as a = hi + lo, |a - hi - lo| <= 2^-48 |a|; each product
+ * accurate to a few 2^-48 of sum |a_k x_k|), which on GB300 outruns the 1/64-rate FP64 pipe;
+ * 0 FP64 (DFMA).  The stencil part and r = F - ... are FP64 in both. */
+int fhmg_problem_set_defect_arith(fhmg_problem p, int mode);
 
 /* FP32 products of the mixed path on the tensor cores (enable != 0, the default): with leaf 64,
  * walks with column tiles of 16 or 32 run as mma.sync m16n8k8 TF32 products split in three

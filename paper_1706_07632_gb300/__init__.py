@@ -63,6 +63,8 @@ _SIGS = {
     "fhmg_problem_set_rtol_reference": (_I, [_P, _I]),
     "fhmg_problem_set_coarse_direct": (_I, [_P, _I]),
     "fhmg_problem_set_tensor_cores": (_I, [_P, _I]),
+    "fhmg_problem_set_defect_arith": (_I, [_P, _I]),
+    "fhmg_hmatvec_df": (_I, [_P, _P, _P, _LL, _I]),
     "fhmg_wsnet_create": (_I, [_I, _I, _c.c_ulonglong, _c.POINTER(_P)]),
     "fhmg_wsnet_destroy": (_I, [_P]),
     "fhmg_wsnet_num_params": (_I, [_P, _c.POINTER(_LL)]),
@@ -192,6 +194,13 @@ class Problem:
         """Solve the coarse-grid correction exactly on the level with n points per dimension
         (n <= 1: recursion to one point, the paper's cycle)."""
         _check(lib().fhmg_problem_set_coarse_direct(self._p, n))
+
+    def set_defect_arith(self, mode):
+        """Outer defect products of the mixed path: 1 double-float (default), 0 FP64."""
+        _check(lib().fhmg_problem_set_defect_arith(self._p, mode))
+
+    def hmatvec_df(self, Y, X, tile=0):
+        _check(lib().fhmg_hmatvec_df(self._p, _ptr(Y), _ptr(X), X.numel() // self.M, tile))
 
     def set_tensor_cores(self, enable=True):
         """FP32 products on the tensor cores (3xTF32 mma.sync) where the column tile allows."""

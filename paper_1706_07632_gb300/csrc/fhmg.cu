@@ -88,6 +88,8 @@ struct fhmg_problem_s {
   DevPanel panel64;  // chunk stream, FP64 matrices
   DevPanel panel32;  // chunk stream, FP32 matrices (mixed path)
   DevPanel panel32m; // the same in the tensor-core layout (build_panel_mma)
+  DevPanel panel64df; // FP64-accurate products in double-float arithmetic (build_panel_df)
+  int defect_df = 1;  // mixed path: the outer FP64 defect's products in double-float arithmetic
   int use_mma = 1;   // FP32 products on the tensor cores where the column tile allows
   double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path) ...
   float* rdiag32 = nullptr; // ... and its FP32 copy (FP32 inner cycles)
@@ -113,7 +115,7 @@ struct fhmg_problem_s {
   // exact coarse-level solve (fhmg_problem_set_coarse_direct), FP64
   int ndirect = 1;              // grid size per dimension solved exactly (1: recursion to one point)
   int lcd = -1;                 // its level index (< nlev - 1), -1: none
-  double* dS = nullptr;         // orthonormal DST-I matrix of that level, n x n
+  double2* dTw = nullptr;       // FFT twiddles exp(-2 pi i j / P), j < P/2, P = 2 (n + 1)
   double* dModeInv = nullptr;   // (D_ii + lam_k I)^{-1}: modes x nb x L x L, DIAG chunk layout
   double* dCA = nullptr;        // scratch, M x points of that level
   double* dCB = nullptr;
@@ -149,11 +151,13 @@ int upload(std::vector<void*>& list, const std::vector<S>& src, const T** out, s
 }
 
 // Uploads the chunk stream of the H-matrix (elem_bytes 8: FP64 products, 4: FP32 products,
-// 0: FP32 products in the tensor-core layout).
+// 0: FP32 products in the tensor-core layout, -1: FP64-accurate double-float products).
 int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, DevPanel& D) {
   fhmg::PanelHost ph;
   if (elem_bytes == 0)
     fhmg::build_panel_mma(h, f, ph);
+  else if (elem_bytes < 0)
+    fhmg::build_panel_df(h, f, ph);
   else
     fhmg::build_panel(h, f, elem_bytes, ph);
   const unsigned char* pkg;
@@ -211,7 +215,8 @@ int walk_status(int s, const std::string& err) {
 
 // Arithmetic of a walk: K64 FP64 storage and products; KSPLIT FP64 storage, FP32 products;
 // K32 FP32 storage and products (inner cycles on well-conditioned grids).
-enum { K64 = 0, KSPLIT = 1, K32 = 2 };
+// KDF: FP64-accurate products in double-float arithmetic (FP64 arrays; products only).
+enum { K64 = 0, KSPLIT = 1, K32 = 2, KDF = 3 };
 
 // Column tile chosen by the autotuner for (kind, mode, ncols), 0 if none (automatic).
 int tuned_tile(fhmg_problem p, int kind, int mode, long long nc) {
@@ -260,8 +265,8 @@ template <typename T>
 fhmg::WalkArgsT<T> matvec_job(fhmg_problem p, int kind, long long nc, const T* X, const T* B, T* OUT,
                               unsigned long long* norm) {
   fhmg::WalkArgsT<T> a{};
-  a.P = kind == K64 ? p->panel64.d : p->panel32.d;
-  if (kind != K64 && p->use_mma && p->panel32m.d.pkg) a.PM = p->panel32m.d;
+  a.P = kind == K64 ? p->panel64.d : kind == KDF ? p->panel64df.d : p->panel32.d;
+  if ((kind == KSPLIT || kind == K32) && p->use_mma && p->panel32m.d.pkg) a.PM = p->panel32m.d;
   a.mode = fhmg::MODE_MATVEC;
   a.geo = Geo{0, 0, 0, nc, 0.0};
   a.ncols = nc;
@@ -291,6 +296,7 @@ int launch_jobs(cudaStream_t st, int kind, std::vector<fhmg::WalkArgsT<double>>&
     while (e < live.size() && live[e].P.L == live[i].P.L && e - i < (size_t)fhmg::kMaxJobs) ++e;
     std::string err;
     int s = kind == KSPLIT ? fhmg::walk_launch_df(st, &live[i], (int)(e - i), &err, nullptr)
+            : kind == KDF  ? fhmg::walk_launch_dfprod(st, &live[i], (int)(e - i), &err, nullptr)
                            : fhmg::walk_launch_dd(st, &live[i], (int)(e - i), &err, nullptr);
     TRY(walk_status(s, err));
     if (counter) ++*counter;
@@ -366,13 +372,19 @@ template <typename T>
 int direct_level(fhmg_problem p, int l, T* E, const T* RC) {
   const LevelData& lv = p->lev[l];
   const int n = lv.N;
-  const long long M = p->M, tot = lv.npts * M;
-  const int blocks = blocks_for(tot);
+  const long long M = p->M;
+  int log2P = 1;
+  while ((1 << log2P) < 2 * (n + 1)) ++log2P;
+  const int P = 1 << log2P;
+  const int thr = std::min(256, std::max(32, P / 2));
+  const size_t smem = 3 * (size_t)P * sizeof(double);
+  // sine transform along x (M * ny lines) and, in 2D, along y (M * nx lines)
+  const unsigned lines_x = (unsigned)(M * (p->dim == 2 ? n : 1)), lines_y = (unsigned)(M * n);
   if (p->dim == 1) {
-    fhmg::sine_transform_kernel<T, double><<<blocks, 256, 0, p->st>>>(RC, p->dCA, p->dS, M, 1, n, 0);
+    fhmg::sine_fft_kernel<T, double><<<lines_x, thr, smem, p->st>>>(RC, p->dCA, p->dTw, M, 1, n, 0, log2P);
   } else {
-    fhmg::sine_transform_kernel<T, double><<<blocks, 256, 0, p->st>>>(RC, p->dCB, p->dS, M, n, n, 0);
-    fhmg::sine_transform_kernel<double, double><<<blocks, 256, 0, p->st>>>(p->dCB, p->dCA, p->dS, M, n, n, 1);
+    fhmg::sine_fft_kernel<T, double><<<lines_x, thr, smem, p->st>>>(RC, p->dCB, p->dTw, M, n, n, 0, log2P);
+    fhmg::sine_fft_kernel<double, double><<<lines_y, thr, smem, p->st>>>(p->dCB, p->dCA, p->dTw, M, n, n, 1, log2P);
     ++p->launches;
   }
   ++p->launches;
@@ -391,10 +403,10 @@ int direct_level(fhmg_problem p, int l, T* E, const T* RC) {
   std::vector<fhmg::WalkArgsT<double>> j{a};
   TRY(launch_jobs(p->st, K64, j, &p->launches));
   if (p->dim == 1) {
-    fhmg::sine_transform_kernel<double, T><<<blocks, 256, 0, p->st>>>(p->dCB, E, p->dS, M, 1, n, 0);
+    fhmg::sine_fft_kernel<double, T><<<lines_x, thr, smem, p->st>>>(p->dCB, E, p->dTw, M, 1, n, 0, log2P);
   } else {
-    fhmg::sine_transform_kernel<double, double><<<blocks, 256, 0, p->st>>>(p->dCB, p->dCA, p->dS, M, n, n, 1);
-    fhmg::sine_transform_kernel<double, T><<<blocks, 256, 0, p->st>>>(p->dCA, E, p->dS, M, n, n, 0);
+    fhmg::sine_fft_kernel<double, double><<<lines_y, thr, smem, p->st>>>(p->dCB, p->dCA, p->dTw, M, n, n, 1, log2P);
+    fhmg::sine_fft_kernel<double, T><<<lines_x, thr, smem, p->st>>>(p->dCA, E, p->dTw, M, n, n, 0, log2P);
     ++p->launches;
   }
   ++p->launches;
@@ -497,8 +509,9 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
                                                                                        u, F, nullptr, dst);
     ++p->launches;
     CK(cudaGetLastError());
+    const int kind = (p->prec == FHMG_MIXED_FP32 && p->defect_df && p->panel64df.d.pkg) ? KDF : K64;
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
-    TRY(walk_matvec<double>(p, K64, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
+    TRY(walk_matvec<double>(p, kind, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
   }
   return read_norm(p, out);
@@ -902,6 +915,7 @@ int fhmg_problem_destroy(fhmg_problem p) {
   for (void* a : p->panel64.allocs) cudaFree(a);
   for (void* a : p->panel32.allocs) cudaFree(a);
   for (void* a : p->panel32m.allocs) cudaFree(a);
+  for (void* a : p->panel64df.allocs) cudaFree(a);
   delete p;
   return FHMG_OK;
 }
@@ -937,6 +951,7 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   if (mixed) {
     if ((st = upload_panel(h->host, h->flat, 4, p->panel32)) != FHMG_OK) return bail(st);
     if (p->L == 64 && (st = upload_panel(h->host, h->flat, 0, p->panel32m)) != FHMG_OK) return bail(st);
+    if ((st = upload_panel(h->host, h->flat, -1, p->panel64df)) != FHMG_OK) return bail(st);
     std::vector<double> rd((size_t)p->nb * p->L);
     for (int i = 0; i < p->nb; ++i)
       for (int r = 0; r < p->L; ++r) rd[(size_t)i * p->L + r] = h->host.dense[h->host.diag[i]].D[(size_t)r * p->L + r];
@@ -1116,17 +1131,15 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   CK(cudaStreamSynchronize(p->st));
   for (void* a : p->dallocs) cudaFree(a);
   p->dallocs.clear();
-  p->dS = p->dModeInv = p->dCA = p->dCB = nullptr;
+  p->dModeInv = p->dCA = p->dCB = nullptr;
+  p->dTw = nullptr;
   p->ndirect = 1;
   p->lcd = -1;
   if (l < 0) return FHMG_OK;
   const LevelData& lv = p->lev[l];
   const int L = p->L, nb = p->nb;
   const double pi = std::acos(-1.0);
-  std::vector<double> S((size_t)n * n), lam1(n), lam(lv.npts), Dd((size_t)nb * L * L);
-  const double sc = std::sqrt(2.0 / (n + 1));
-  for (int j = 0; j < n; ++j)
-    for (int k = 0; k < n; ++k) S[(size_t)j * n + k] = sc * std::sin(pi * (j + 1) * (k + 1) / (n + 1));
+  std::vector<double> lam1(n), lam(lv.npts), Dd((size_t)nb * L * L);
   for (int q = 0; q < n; ++q) {
     const double sn = std::sin(pi * (q + 1) / (2.0 * (n + 1)));
     lam1[q] = 4.0 * lv.inv_h2 * sn * sn;
@@ -1134,11 +1147,17 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   for (long long m = 0; m < lv.npts; ++m) lam[m] = p->dim == 1 ? lam1[m] : lam1[m / n] + lam1[m % n];
   for (int i = 0; i < nb; ++i)
     std::memcpy(&Dd[(size_t)i * L * L], p->H->host.dense[p->H->host.diag[i]].D.data(), sizeof(double) * L * L);
-  const double *dS, *dlam, *dDd;
-  TRY(upload(p->dallocs, S, &dS, nullptr));
+  const double *dlam, *dDd, *dtw;
   TRY(upload(p->dallocs, lam, &dlam, nullptr));
   TRY(upload(p->dallocs, Dd, &dDd, nullptr));
-  p->dS = const_cast<double*>(dS);
+  const int P = 2 * (n + 1);
+  std::vector<double> tw(P);  // (cos, -sin)(2 pi j / P), j < P/2
+  for (int j = 0; j < P / 2; ++j) {
+    tw[2 * j] = std::cos(2.0 * pi * j / P);
+    tw[2 * j + 1] = -std::sin(2.0 * pi * j / P);
+  }
+  TRY(upload(p->dallocs, tw, &dtw, nullptr));
+  p->dTw = reinterpret_cast<double2*>(const_cast<double*>(dtw));
   TRY(dalloc(p->dallocs, &p->dModeInv, (size_t)lv.npts * nb * L * L));
   TRY(dalloc(p->dallocs, &p->dCA, (size_t)lv.npts * p->M));
   TRY(dalloc(p->dallocs, &p->dCB, (size_t)lv.npts * p->M));
@@ -1150,6 +1169,13 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   CK(cudaStreamSynchronize(p->st));
   p->ndirect = n;
   p->lcd = l;
+  return FHMG_OK;
+}
+
+int fhmg_problem_set_defect_arith(fhmg_problem p, int mode) {
+  TRY(check_dims(p));
+  if (mode != 0 && mode != 1) return fail(FHMG_EINVAL, "defect arithmetic must be 0 (FP64) or 1 (double-float)");
+  p->defect_df = mode;
   return FHMG_OK;
 }
 
@@ -1235,6 +1261,21 @@ int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols
   std::vector<fhmg::WalkArgsT<double>> j{matvec_job<double>(p, KSPLIT, ncols, X, Y, Y, nullptr)};
   j[0].tile = tile;
   TRY(launch_jobs(p->st, KSPLIT, j, &p->launches));
+  scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
+  ++p->launches;
+  CK(cudaGetLastError());
+  return FHMG_OK;
+}
+
+int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols, int tile) {
+  TRY(check_dims(p));
+  if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "double-float products need a mixed-precision problem");
+  if (!X || !Y || ncols < 0 || X == Y || (tile != 0 && tile != 4 && tile != 8 && tile != 16))
+    return fail(FHMG_EINVAL, "bad arguments");
+  CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
+  std::vector<fhmg::WalkArgsT<double>> j{matvec_job<double>(p, KDF, ncols, X, Y, Y, nullptr)};
+  j[0].tile = tile;
+  TRY(launch_jobs(p->st, KDF, j, &p->launches));
   scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
   ++p->launches;
   CK(cudaGetLastError());

@@ -659,6 +659,76 @@ void build_panel_mma(const HostH& h, const FlatH& f, PanelHost& out) {
   }
 }
 
+void build_panel_df(const HostH& h, const FlatH& f, PanelHost& out) {
+  const int L = f.L, nb = f.nb;
+  out = PanelHost();
+  out.cptr.assign(nb + 1, 0);
+  int maxdist = 0;
+  for (int i = 0; i < nb; ++i)
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) maxdist = std::max(maxdist, i - f.dlist_col[d]);
+  out.W = std::min(8, maxdist + 1);
+  out.far = maxdist + 1 > out.W;
+  auto add_chunk = [&](int type, int count, int aux, size_t bytes) -> size_t {
+    size_t off = out.pkg.size();
+    size_t nbytes = pad16(bytes);
+    out.pkg.resize(off + nbytes, 0);
+    out.chunks.push_back(type | (count << 4));
+    out.chunks.push_back(aux);
+    out.chunks.push_back((int)nbytes);
+    out.chunks.push_back((int)(off / 16));
+    out.slot_bytes = std::max(out.slot_bytes, (int)nbytes);
+    return off;
+  };
+  // entry (k, r) of an R x K chunk matrix: hi at float index ((k/4) R + r) 4 + k%4 of the hi block,
+  // lo at the same index of the lo block that follows it (R K floats later)
+  auto put = [&](size_t off, int k, int r, int R, int K, double v) {
+    const float hi = (float)v;
+    const float lo = (float)(v - (double)hi);
+    const size_t idx = ((size_t)(k / 4) * R + r) * 4 + k % 4;
+    std::memcpy(&out.pkg[off + idx * 4], &hi, 4);
+    std::memcpy(&out.pkg[off + ((size_t)R * K + idx) * 4], &lo, 4);
+  };
+  for (int i = 0; i < nb; ++i) {
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) {
+      const double* D = &f.dense_data[(size_t)f.dlist_blk[d] * L * L];
+      size_t off = add_chunk(CH_DENSE, L, f.dlist_col[d], (size_t)L * L * 8);
+      for (int k = 0; k < L; ++k)
+        for (int r = 0; r < L; ++r) put(off, k, r, L, L, D[(size_t)r * L + k]);
+    }
+    const int K = f.uptr[i + 1] - f.uptr[i];
+    for (int k0 = 0; k0 < K; k0 += L) {
+      const int kc = std::min(L, K - k0);
+      const int kp = (kc + 3) / 4 * 4;
+      size_t off = add_chunk(CH_UPART, kp, k0, (size_t)kp * L * 8 + (size_t)kp * 4);
+      for (int kk = 0; kk < kc; ++kk)
+        for (int r = 0; r < L; ++r) put(off, kk, r, L, kp, f.udata[f.uoff[i] + (size_t)r * K + k0 + kk]);
+      for (int kk = 0; kk < kp; ++kk) {
+        int z = f.uz[f.uptr[i] + k0 + (kk < kc ? kk : 0)];
+        std::memcpy(&out.pkg[off + (size_t)kp * L * 8 + (size_t)kk * 4], &z, 4);
+      }
+    }
+    {
+      const double* D = &f.dense_data[(size_t)f.diag_blk[i] * L * L];
+      size_t off = add_chunk(CH_DIAG, L, i, (size_t)L * L * 8);
+      for (int k = 0; k < L; ++k)
+        for (int r = 0; r < L; ++r) put(off, k, r, L, L, D[(size_t)r * L + k]);
+    }
+    const int Kv = f.vptr[i + 1] - f.vptr[i];
+    for (int k0 = 0; k0 < Kv; k0 += L) {
+      const int kc = std::min(L, Kv - k0);
+      size_t off = add_chunk(CH_VPART, kc, k0, (size_t)kc * L * 8 + (size_t)kc * 4);
+      for (int kk = 0; kk < kc; ++kk)
+        for (int c = 0; c < L; ++c) put(off, c, kk, kc, L, f.vdata[f.voff[i] + (size_t)(k0 + kk) * L + c]);
+      for (int kk = 0; kk < kc; ++kk) {
+        int code = 2 * f.vz[f.vptr[i] + k0 + kk] + f.vinit[f.vptr[i] + k0 + kk];
+        std::memcpy(&out.pkg[off + (size_t)kc * L * 8 + (size_t)kk * 4], &code, 4);
+      }
+    }
+    out.chunks[out.chunks.size() - 4] |= 1 << 12;
+    out.cptr[i + 1] = (int)(out.chunks.size() / 4);
+  }
+}
+
 void to_mma_layout(const double* A, int L, bool zero_diag, float* out) {
   const int nkb = (L + 15) / 16;
   std::vector<unsigned char> buf((size_t)nkb * 16 * nkb * 16 * 2 * 4, 0);

@@ -111,6 +111,12 @@ void build_panel_mma(const HostH& h, const FlatH& f, PanelHost& out);
 // The row-major L x L matrix A in that layout (hi/lo pairs, L*L*2 floats for L a multiple of 16).
 void to_mma_layout(const double* A, int L, bool zero_diag, float* out);
 
+// The same stream for FP64-accurate products in double-float arithmetic (pairs of floats, hi =
+// fl32(a), lo = fl32(a - hi), |a - hi - lo| <= 2^-48 |a|): the FP32 vector-interleaved layout of the
+// hi parts of a chunk matrix (R x K, K padded to a multiple of 4), then the lo parts in the same
+// layout, then the chunk's int indices.  DIAG blocks keep their diagonal (products only).
+void build_panel_df(const HostH& h, const FlatH& f, PanelHost& out);
+
 
 // Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
 // Returns 0 on success, < 0 on invalid arguments.

@@ -34,6 +34,10 @@ int walk_launch_dd(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, st
 int walk_launch_df(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 int walk_launch_ff(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std::string* err, int* tile_used);
 
+// FP64-accurate products (MODE_MATVEC) in double-float arithmetic, walk_dfd.cu: the jobs' P is the
+// build_panel_df stream; tile 4, 8 or 16 (0: automatic).
+int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
+
 // Tensor-core walks (FP32 products, leaf 64, TC 16 or 32), walk_mma.cu.  B.ns is chosen here.
 int mma_launch_df(cudaStream_t st, WalkBatch<double, float>& B, int TC, int mode, std::string* err);
 int mma_launch_ff(cudaStream_t st, WalkBatch<float, float>& B, int TC, int mode, std::string* err);

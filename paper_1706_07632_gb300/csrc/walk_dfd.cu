@@ -1,0 +1,104 @@
+// Launcher of the double-float defect product (hdf_kernel, df.cuh): FP64 arrays, FP64-accurate
+// H-matrix products in FP32-pair arithmetic.
+#include <algorithm>
+#include <string>
+
+#include "df.cuh"
+#include "walk.h"
+
+namespace fhmg {
+namespace {
+
+constexpr int kDfBlock = 256 + 32;
+constexpr size_t kDfSmemMax = 227 * 1024;
+
+template <int L, int TC>
+int df_launch_t(cudaStream_t st, WalkBatch<double, float>& B, std::string* err) {
+  auto kern = hdf_kernel<L, TC>;
+  const size_t other = df_smem(L, TC, B.pool, B.W, B.slot_bytes, 0).total + 64;
+  int ns = other < kDfSmemMax ? (int)((kDfSmemMax - other) / (size_t)B.slot_bytes) : 0;
+  ns = std::min(ns, 8);
+  if (ns < 2) {
+    *err = "double-float walk: no room for two chunk slots in shared memory";
+    return 2;
+  }
+  B.ns = ns;
+  const size_t smem = df_smem(L, TC, B.pool, B.W, B.slot_bytes, ns).total;
+  static size_t configured = 48 * 1024;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+      return 1;
+    }
+    configured = smem;
+  }
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDfBlock, smem) != cudaSuccess || occ < 1) occ = 1;
+  if (B.ntiles <= 0) return 0;
+  const long long grid = std::min<long long>(B.ntiles, 152LL * occ);
+  kern<<<(unsigned)grid, kDfBlock, smem, st>>>(B);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = std::string("double-float walk launch: ") + cudaGetErrorString(e);
+    return 1;
+  }
+  return 0;
+}
+
+}  // namespace
+
+int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used) {
+  if (njobs < 1 || njobs > kMaxJobs) {
+    *err = "double-float walk needs 1.." + std::to_string(kMaxJobs) + " jobs";
+    return 2;
+  }
+  const int L = jobs[0].P.L;
+  WalkBatch<double, float> B;
+  B.njobs = njobs;
+  B.pool = 0;
+  B.W = 1;
+  B.slot_bytes = 16;
+  B.err = jobs[0].err;
+  long long cols = 0;
+  for (int j = 0; j < njobs; ++j) {
+    if (jobs[j].P.L != L || jobs[j].mode != MODE_MATVEC) {
+      *err = "double-float walk: product jobs of one leaf size only";
+      return 2;
+    }
+    B.pool = std::max(B.pool, jobs[j].P.pool);
+    B.W = std::max(B.W, jobs[j].P.W);
+    B.slot_bytes = std::max(B.slot_bytes, jobs[j].P.slot_bytes);
+    cols += jobs[j].ncols;
+  }
+  // column tile: 16 once the columns give every SM a tile of 16, else 8, else 4
+  int TC = jobs[0].tile;
+  if (TC != 4 && TC != 8 && TC != 16) TC = cols >= 16LL * 152 ? 16 : cols >= 8LL * 152 ? 8 : 4;
+  if (tile_used) *tile_used = TC;
+  long long tiles = 0;
+  for (int j = 0; j < njobs; ++j) {
+    WalkJob<double, float>& J = B.job[j];
+    J.P = jobs[j].P;
+    J.geo = jobs[j].geo;
+    J.ncols = jobs[j].ncols;
+    J.tile0 = tiles;
+    J.X = jobs[j].X;
+    J.B = jobs[j].B;
+    J.OUT = jobs[j].OUT;
+    J.Dinv = nullptr;
+    J.dinv_cstride = 0;
+    J.ddiag = nullptr;
+    J.norm = jobs[j].norm;
+    tiles += (jobs[j].ncols + TC - 1) / TC;
+  }
+  B.ntiles = tiles;
+  B.ns = 2;
+#define FHMG_DF(LL, TT) \
+  if (L == LL && TC == TT) return df_launch_t<LL, TT>(st, B, err);
+  FHMG_DF(64, 4) FHMG_DF(64, 8) FHMG_DF(64, 16) FHMG_DF(32, 4) FHMG_DF(32, 8) FHMG_DF(32, 16)
+#undef FHMG_DF
+  *err = "no double-float walk for leaf " + std::to_string(L);
+  return 2;
+}
+
+}  // namespace fhmg

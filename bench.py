@@ -15,11 +15,12 @@ paper's recursion to one point instead.
 value     = DOF * K_ref * ranks / (device time per solve), K_ref = the FP64 V(1,1) cycle count of
             the workload (8 for the headline), so every arm and path is compared on
             time-to-solution in one unit.  value is the mixed-precision path (defect correction,
-            FP32 H-matrix products, FP64 defect); the FP64 path is reported beside it.
+            FP32 H-matrix products inside the cycles, an FP64-accurate outer defect whose products
+            run in double-float arithmetic); the FP64 path is reported beside it.
 e2e       = the same metric through fhmg_solve_host (pinned host buffers; H2D of u and f and D2H
             of u inside the timed region).
 roofline  = the dominant kernel of the headline step -- the finest-grid smoother half-sweeps or the
-            FP64 outer defect, whichever has the larger share -- timed live with CUDA events on the
+            outer defect, whichever has the larger share -- timed live with CUDA events on the
             launching stream inside the timed solves (the other one: roofline_secondary).
 cpu_baseline / --impl reference = the oracle's direct solve (implicit time stepping with the dense
             L1 history sum, numpy/OpenBLAS) of the same workload on the host cores.
@@ -43,6 +44,9 @@ sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # 1.258: DFMA units x clock (a DFMA loop measured 1.202)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: FFMA units x clock (an FFMA loop measured 75.1)
+# double-float multiply-add = 11 FP32 instructions (TwoProd by FMA, two cross-term FMAs, TwoSum,
+# low-word update): 2 algorithmic flops per 11 FP32 lane-instructions
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / 11 / 1e12  # 7.32
 REF_CYCLES_1D = 8   # FP64 V(1,1) cycles to 1e-8 on the headline workload, measured on GB300
 
 
@@ -364,17 +368,23 @@ def roofline(H, r, ncols_avg, kind):
             "share_of_step": c["smooth_ms"] / r["ms"] if r["ms"] > 0 else None}
 
 
-def roofline_defect(H, r, ncols, traffic=None):
-    """Finest-grid FP64 defect products (Algorithm 3 over ncols columns), timed live."""
+def roofline_defect(H, r, ncols, arith="fp64", traffic=None):
+    """Finest-grid defect products (Algorithm 3 over ncols columns), timed live: FP64 (DFMA) or
+    FP64-accurate double-float arithmetic on the FP32 pipe (the mixed path's default)."""
     c = r["cnt"]
     n = max(c["defect_launches"], 1)
     ms = c["defect_ms"] / n
     flops_launch = H.flops_per_column() * ncols
     achieved = flops_launch / (ms / 1e3) / 1e12
-    return {"kernel": f"hpanel_kernel<double,double,64,*,MATVEC> (finest-grid FP64 defect, {ncols} columns)",
-            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_note": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured 1.202)",
+    if arith == "df":
+        kern = f"hdf_kernel<64,*> (finest-grid FP64-accurate defect, double-float, {ncols} columns)"
+        peak, note = DF_PEAK_TFLOPS, ("152 SMs x 128 FP32 lanes/clk x 2.07 GHz x 2 flop per 11-instruction "
+                                      "double-float multiply-add")
+    else:
+        kern = f"hpanel_kernel<double,double,64,*,MATVEC> (finest-grid FP64 defect, {ncols} columns)"
+        peak, note = FP64_PEAK_TFLOPS, "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured 1.202)"
+    return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_note": note,
             "traffic": traffic, "avg_launch_ms": ms, "launches_timed": c["defect_launches"],
             "algorithmic_flops_per_launch": flops_launch,
             "share_of_step": c["defect_ms"] / r["ms"] if r["ms"] > 0 else None}
@@ -471,7 +481,7 @@ def main():
 
     # the headline step's dominant kernel: the FP32-product smoother or the FP64 outer defect
     rl_s = roofline(H, res["mixed"], a.N / 2.0, "mixed")
-    rl_d = roofline_defect(H, res["mixed"], a.N)
+    rl_d = roofline_defect(H, res["mixed"], a.N, "df")
     rl_head = dominant(rl_s, rl_d)
     rl_second = rl_d if rl_head is rl_s else rl_s
     if rank == 0:
@@ -479,7 +489,8 @@ def main():
                 "unit": "DOF*cycles/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": head["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": workload(a),
-                "headline": "mixed precision: FP64 defect correction around V-cycles with FP32 H-matrix products",
+                "headline": ("mixed precision: defect correction with an FP64-accurate (double-float) outer defect around "
+                             "V-cycles with FP32 H-matrix products (3xTF32 tensor cores on wide tiles)"),
                 "cycle_unit": f"FP64 V(1,1) cycles to relres {a.rtol:g} on this workload = {k_ref:.0f}",
                 "fp64": summary(res["fp64"], a.steps), "mixed": summary(res["mixed"], a.steps),
                 "speedup_mixed_vs_fp64": res["fp64"]["time_to_rtol_s"] / res["mixed"]["time_to_rtol_s"],

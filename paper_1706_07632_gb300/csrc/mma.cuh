@@ -6,8 +6,9 @@
 //   DIAG   X_i = Dinv Y (smoother) / Y -= D_ii X_i (product)
 //   VPART  Z (+)= V_i X_i     (K' x 64) x (64 x TC)
 // run as mma.sync m16n8k8 TF32 with FP32 accumulation, each product split in three,
-// hi*hi + hi*lo + lo*hi (hi = tf32(a), lo = tf32(a - hi)), which keeps FP32 accuracy.  The
-// matrices arrive pre-split in the fragment layout of build_panel_mma; x tiles are split on load.
+// hi*hi + hi*lo + lo*hi (hi = tf32(a), lo = tf32(a - hi)), which keeps FP32 accuracy; each term
+// has its own accumulator.  The matrices arrive pre-split in the fragment layout of
+// build_panel_mma; x tiles are split once when written (tiles of <= 16 columns) or on load.
 //
 // Warps: 8 consumer warps, warp w owns row tile rt = w % 4 (16 rows of the leaf) and column half
 // w / 4 (TC / 2 columns = TC / 16 n-tiles of 8).  Lane (g, t) = (lane / 4, lane % 4) holds the
@@ -27,12 +28,17 @@ constexpr int kMmaLP = 80;  // padded x-tile column (floats): 8 columns x 4 lane
 struct MmaSmem {
   size_t ysm, ring, zp, bar, ebar, cbar, desc, flag, total;
 };
+// x tiles (y of the current leaf, the ring of recent x) of tiles up to 16 columns are kept as TF32
+// hi/lo pairs ([hi: TC x LP][lo: TC x LP] per tile), split once when written; wider tiles keep
+// one float per entry and split on every load (their shared memory would not hold the pairs).
+__host__ __device__ inline int mma_xsplit(int TC) { return TC <= 16 ? 2 : 1; }
 __host__ __device__ inline MmaSmem mma_smem(int TC, int pool, int W, int slot_bytes, int ns) {
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t tile = (size_t)mma_xsplit(TC) * TC * kMmaLP * 4;
   MmaSmem s;
   s.ysm = a16((size_t)ns * slot_bytes);
-  s.ring = a16(s.ysm + (size_t)TC * kMmaLP * 4);
-  s.zp = a16(s.ring + (size_t)W * TC * kMmaLP * 4);
+  s.ring = a16(s.ysm + tile);
+  s.zp = a16(s.ring + (size_t)W * tile);
   s.bar = a16(s.zp + (size_t)pool * TC * 4);
   s.ebar = s.bar + 8 * (size_t)ns;
   s.cbar = s.ebar + 8 * (size_t)ns;
@@ -56,24 +62,38 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// c += A B over one 16-block of the reduction: A from four 16-byte vectors (hi/lo of rows g and
-// g + 8), B from one float4 of the lane's column (split here); two k-steps, three products each.
-__device__ __forceinline__ void mma_block(float (&c)[4], const float4 h0, const float4 h1, const float4 l0,
-                                          const float4 l1, const float4 xv) {
-  const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-  uint32_t bh[4], bl[4];
+// One accumulator per product term (lo*hi, hi*lo, hi*hi): the mma chains of a chunk are then
+// three independent ones; the terms are summed, small ones first, where the products are used.
+struct Acc3 {
+  float lh[4], hl[4], hh[4];
+};
+__device__ __forceinline__ void acc_zero(Acc3& a) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a.lh[j] = a.hl[j] = a.hh[j] = 0.f;
+}
+__device__ __forceinline__ float acc_sum(const Acc3& a, int j) { return (a.lh[j] + a.hl[j]) + a.hh[j]; }
+
+// TF32 hi/lo words of four values
+__device__ __forceinline__ void split4(const float4 v, uint32_t (&bh)[4], uint32_t (&bl)[4]) {
+  const float xs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     bh[e] = to_tf32(xs[e]);
     bl[e] = to_tf32(xs[e] - __uint_as_float(bh[e]));
   }
-  // step 0: k' = t -> e 0, k' = t + 4 -> e 1; step 1: e 2, e 3
-  mma_tf32(c, __float_as_uint(l0.x), __float_as_uint(l1.x), __float_as_uint(l0.y), __float_as_uint(l1.y), bh[0], bh[1]);
-  mma_tf32(c, __float_as_uint(h0.x), __float_as_uint(h1.x), __float_as_uint(h0.y), __float_as_uint(h1.y), bl[0], bl[1]);
-  mma_tf32(c, __float_as_uint(h0.x), __float_as_uint(h1.x), __float_as_uint(h0.y), __float_as_uint(h1.y), bh[0], bh[1]);
-  mma_tf32(c, __float_as_uint(l0.z), __float_as_uint(l1.z), __float_as_uint(l0.w), __float_as_uint(l1.w), bh[2], bh[3]);
-  mma_tf32(c, __float_as_uint(h0.z), __float_as_uint(h1.z), __float_as_uint(h0.w), __float_as_uint(h1.w), bl[2], bl[3]);
-  mma_tf32(c, __float_as_uint(h0.z), __float_as_uint(h1.z), __float_as_uint(h0.w), __float_as_uint(h1.w), bh[2], bh[3]);
+}
+
+// c += A B over one 16-block of the reduction: A from four 16-byte vectors (hi/lo of rows g and
+// g + 8), B as the hi/lo words of the lane's four reduction indices; two k-steps, three products
+// each (step 0: k' = t -> e 0, k' = t + 4 -> e 1; step 1: e 2, e 3).
+__device__ __forceinline__ void mma_block(Acc3& c, const float4 h0, const float4 h1, const float4 l0, const float4 l1,
+                                          const uint32_t (&bh)[4], const uint32_t (&bl)[4]) {
+  mma_tf32(c.lh, __float_as_uint(l0.x), __float_as_uint(l1.x), __float_as_uint(l0.y), __float_as_uint(l1.y), bh[0], bh[1]);
+  mma_tf32(c.hl, __float_as_uint(h0.x), __float_as_uint(h1.x), __float_as_uint(h0.y), __float_as_uint(h1.y), bl[0], bl[1]);
+  mma_tf32(c.hh, __float_as_uint(h0.x), __float_as_uint(h1.x), __float_as_uint(h0.y), __float_as_uint(h1.y), bh[0], bh[1]);
+  mma_tf32(c.lh, __float_as_uint(l0.z), __float_as_uint(l1.z), __float_as_uint(l0.w), __float_as_uint(l1.w), bh[2], bh[3]);
+  mma_tf32(c.hl, __float_as_uint(h0.z), __float_as_uint(h1.z), __float_as_uint(h0.w), __float_as_uint(h1.w), bl[2], bl[3]);
+  mma_tf32(c.hh, __float_as_uint(h0.z), __float_as_uint(h1.z), __float_as_uint(h0.w), __float_as_uint(h1.w), bh[2], bh[3]);
 }
 
 // The four A vectors of (row tile rt, k-block kb) of a chunk matrix with nkb k-blocks.
@@ -162,6 +182,29 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
   const int rt = w & 3;                 // row tile
   const int cb = (w >> 2) * (TC / 2);   // first column of this warp
   const int g = lane >> 2, tq = lane & 3;
+  constexpr int XS = TC <= 16 ? 2 : 1;        // mma_xsplit(TC)
+  constexpr int TS = XS * TC * LP;            // floats per x tile
+  // B operand of column col, k-block kb from an x tile (pre-split, or split here)
+  auto load_b = [&](const float* tile, int col, int kb, uint32_t(&bh)[4], uint32_t(&bl)[4]) {
+    const float* p = tile + col * LP + kb * 16 + 4 * tq;
+    if (XS == 2) {
+      const float4 hv = *reinterpret_cast<const float4*>(p);
+      const float4 lv = *reinterpret_cast<const float4*>(p + TC * LP);
+      bh[0] = __float_as_uint(hv.x), bh[1] = __float_as_uint(hv.y), bh[2] = __float_as_uint(hv.z), bh[3] = __float_as_uint(hv.w);
+      bl[0] = __float_as_uint(lv.x), bl[1] = __float_as_uint(lv.y), bl[2] = __float_as_uint(lv.z), bl[3] = __float_as_uint(lv.w);
+    } else {
+      split4(*reinterpret_cast<const float4*>(p), bh, bl);
+    }
+  };
+  auto store_x = [&](float* tile, int col, int row, float v) {
+    if (XS == 2) {
+      const uint32_t h = to_tf32(v);
+      tile[col * LP + row] = __uint_as_float(h);
+      tile[TC * LP + col * LP + row] = __uint_as_float(to_tf32(v - __uint_as_float(h)));
+    } else {
+      tile[col * LP + row] = v;
+    }
+  };
   uint32_t cbphase = 0;
   auto give_up = [&](bool ok) -> bool {
     if (__all_sync(0xffffffffu, ok)) return false;
@@ -241,19 +284,20 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
 
     for (int i = 0; i < nb; ++i) {
       T rhs[NTL][4], xcur[NTL][4], ddv[2];
-      float acc[NTL][4];
+      Acc3 acc[NTL];
 #pragma unroll
-      for (int nt = 0; nt < NTL; ++nt)
+      for (int nt = 0; nt < NTL; ++nt) {
+        acc_zero(acc[nt]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           rhs[nt][j] = bn[nt][j];
           xcur[nt][j] = xn[nt][j];
-          acc[nt][j] = 0.f;
         }
+      }
       ddv[0] = dn[0];
       ddv[1] = dn[1];
       load_rhs(i + 1);
-      float* xr_i = ring + (size_t)(i % W) * TC * LP;  // x_i tile [column][k]
+      float* xr_i = ring + (size_t)(i % W) * TS;  // x_i tile [column][k]
       for (bool leaf_done = false; !leaf_done;) {
         if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag))) return;
         const int4 cd = sdesc[cslot];
@@ -262,15 +306,16 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
         const unsigned char* buf = slots + (size_t)cslot * B.slot_bytes;
         const float4* A = reinterpret_cast<const float4*>(buf);
         if (type == PK_DENSE) {
-          const float* xr = ring + (size_t)(cd.y % W) * TC * LP;
+          const float* xr = ring + (size_t)(cd.y % W) * TS;
 #pragma unroll
           for (int kb = 0; kb < 4; ++kb) {
             float4 h0, h1, l0, l1;
             load_a(A, rt, kb, 4, lane, h0, h1, l0, l1);
 #pragma unroll
             for (int nt = 0; nt < NTL; ++nt) {
-              const float4 xv = *reinterpret_cast<const float4*>(xr + (cb + nt * 8 + g) * LP + kb * 16 + 4 * tq);
-              mma_block(acc[nt], h0, h1, l0, l1, xv);
+              uint32_t bh[4], bl[4];
+              load_b(xr, cb + nt * 8 + g, kb, bh, bl);
+              mma_block(acc[nt], h0, h1, l0, l1, bh, bl);
             }
           }
         } else if (type == PK_UPART) {
@@ -285,8 +330,9 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
 #pragma unroll
               for (int nt = 0; nt < NTL; ++nt) {
                 const int c = cb + nt * 8 + g;
-                const float4 zv = make_float4(zp[zi.x * TC + c], zp[zi.y * TC + c], zp[zi.z * TC + c], zp[zi.w * TC + c]);
-                mma_block(acc[nt], h0, h1, l0, l1, zv);
+                uint32_t bh[4], bl[4];
+                split4(make_float4(zp[zi.x * TC + c], zp[zi.y * TC + c], zp[zi.z * TC + c], zp[zi.w * TC + c]), bh, bl);
+                mma_block(acc[nt], h0, h1, l0, l1, bh, bl);
               }
             }
           }
@@ -298,11 +344,12 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const int h = j >> 1, e = j & 1;
-              rhs[nt][j] -= (T)acc[nt][j];
+              rhs[nt][j] -= (T)acc_sum(acc[nt], j);
               const int col = cb + nt * 8 + 2 * tq + e, row = rt * 16 + g + 8 * h;
-              opnd[col * LP + row] = (float)(MODE == MODE_SMOOTH ? rhs[nt][j] : xcur[nt][j]);
-              acc[nt][j] = 0.f;
+              store_x(opnd, col, row, (float)(MODE == MODE_SMOOTH ? rhs[nt][j] : xcur[nt][j]));
             }
+#pragma unroll
+          for (int nt = 0; nt < NTL; ++nt) acc_zero(acc[nt]);
           if (!consumer_sync()) return;  // the operand is complete
 #pragma unroll
           for (int kb = 0; kb < 4; ++kb) {
@@ -310,8 +357,9 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
             load_a(A, rt, kb, 4, lane, h0, h1, l0, l1);
 #pragma unroll
             for (int nt = 0; nt < NTL; ++nt) {
-              const float4 xv = *reinterpret_cast<const float4*>(opnd + (cb + nt * 8 + g) * LP + kb * 16 + 4 * tq);
-              mma_block(acc[nt], h0, h1, l0, l1, xv);
+              uint32_t bh[4], bl[4];
+              load_b(opnd, cb + nt * 8 + g, kb, bh, bl);
+              mma_block(acc[nt], h0, h1, l0, l1, bh, bl);
             }
           }
 #pragma unroll
@@ -322,11 +370,11 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
               const int col = cb + nt * 8 + 2 * tq + e, row = rt * 16 + g + 8 * h;
               const long long at = (long long)(i * L + row) * ld + pcol[nt][e];
               if (MODE == MODE_SMOOTH) {
-                const T x = (T)acc[nt][j] + ddv[h] * rhs[nt][j];
-                xr_i[col * LP + row] = (float)x;
+                const T x = (T)acc_sum(acc[nt], j) + ddv[h] * rhs[nt][j];
+                store_x(xr_i, col, row, (float)x);
                 if (vcol[nt][e]) X[at] = x;
               } else {
-                const T o = rhs[nt][j] - (T)acc[nt][j] - ddv[h] * xcur[nt][j];
+                const T o = rhs[nt][j] - (T)acc_sum(acc[nt], j) - ddv[h] * xcur[nt][j];
                 if (vcol[nt][e]) {
                   if (J.OUT) J.OUT[at] = o;
                   const double av = fabs((double)o);
@@ -339,19 +387,18 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
           const int nrt = (cnt + 15) / 16;
           const int* vz = reinterpret_cast<const int*>(buf + (size_t)nrt * 4 * 4 * 32 * 16);
           if (rt < nrt) {
-            float zacc[NTL][4];
+            Acc3 zacc[NTL];
 #pragma unroll
-            for (int nt = 0; nt < NTL; ++nt)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) zacc[nt][j] = 0.f;
+            for (int nt = 0; nt < NTL; ++nt) acc_zero(zacc[nt]);
 #pragma unroll
             for (int kb = 0; kb < 4; ++kb) {
               float4 h0, h1, l0, l1;
               load_a(A, rt, kb, 4, lane, h0, h1, l0, l1);
 #pragma unroll
               for (int nt = 0; nt < NTL; ++nt) {
-                const float4 xv = *reinterpret_cast<const float4*>(xr_i + (cb + nt * 8 + g) * LP + kb * 16 + 4 * tq);
-                mma_block(zacc[nt], h0, h1, l0, l1, xv);
+                uint32_t bh[4], bl[4];
+                load_b(xr_i, cb + nt * 8 + g, kb, bh, bl);
+                mma_block(zacc[nt], h0, h1, l0, l1, bh, bl);
               }
             }
 #pragma unroll
@@ -363,7 +410,8 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
                 if (zr < cnt) {
                   const int code = vz[zr];
                   float* z = zp + (code >> 1) * TC + cb + nt * 8 + 2 * tq + e;
-                  *z = (code & 1) ? zacc[nt][j] : *z + zacc[nt][j];
+                  const float v = acc_sum(zacc[nt], j);
+                  *z = (code & 1) ? v : *z + v;
                 }
               }
           }

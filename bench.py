@@ -84,7 +84,7 @@ def workload(a):
     gamma = (2 - a.alpha) / a.alpha
     return {"workload": f"1D H-matrix, N={a.N}, M={a.M}, alpha={a.alpha}, gamma={gamma:.4g}, leaf 64, tol 1e-10, "
                         f"V(1,1) to relres {a.rtol:g}",
-            "coarse_solve": coarse_desc(coarse_direct(a, 1, a.N)),
+            "coarse_solve": coarse_desc(coarse_direct(a, 1, a.N)), "tiles": "autotuned (fhmg_problem_autotune)",
             "dim": 1, "N": a.N, "M": a.M, "alpha": a.alpha, "gamma": gamma, "leaf": 64, "tol": 1e-10,
             "cycle": "V(1,1)", "rtol": a.rtol, "source": "manufactured t^alpha sin(pi x)",
             "l2": "inputs larger than L2 (u, f 134 MB each)"}
@@ -231,6 +231,7 @@ def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, di
     for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
         P = fh.Problem(H, dim, N, 1.0, prec, stream)
         P.set_coarse_direct(nc)
+        P.autotune()  # column tiles timed per (kind, mode, columns); setup, untimed
         r = timed_solves(P, f, steps, warmup, rtol, stream, dist)
         r["P"] = P
         r["time_to_rtol_s"] = r["ms"] / steps / 1e3

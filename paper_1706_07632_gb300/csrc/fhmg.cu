@@ -1080,7 +1080,7 @@ int fhmg_problem_autotune(fhmg_problem p) {
             fhmg::WalkArgsT<double> job =
                 mode == fhmg::MODE_SMOOTH
                     ? smooth_job<double>(p, l, kind, Geo{p->dim, lv.N, (int)ci, lv.npts, lv.inv_h2}, nc, p->Rs, p->Rs)
-                    : matvec_job<double>(p, kind, nc, p->Xs, p->Rs, p->Rs, nullptr);
+                    : matvec_job<double>(p, kind, nc, p->Rs, p->Rs, nullptr, nullptr);
             job.tile = tc;
             float ms = 0.f;
             int s2 = time_jobs(kind, job, &ms);

@@ -95,13 +95,14 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
   for (int j = 0; j < njobs; ++j) total_cols += jobs[j].ncols;
   if constexpr (sizeof(TM) == 4) {
     // FP32 products on the tensor cores: leaf 64, tile 16 or 32 (tile 16 once the columns fill
-    // about half the SMs with 16 each, 32 once they fill every SM with 32)
+    // 128 SMs with 16 each -- below that the SIMT walk with narrower tiles on every SM is faster,
+    // e.g. 0.36 vs 0.52 ms at 1024 columns x M = 4096 -- and 32 once they fill every SM with 32)
     bool mma_ok = L == 64;
     for (int j = 0; j < njobs; ++j)
       mma_ok = mma_ok && jobs[j].PM.pkg != nullptr && !jobs[j].PM.far && jobs[j].dinv_cstride == 0;
     if (mma_ok) {
       int tcm = jobs[0].tile;
-      if (tcm == 0) tcm = total_cols >= 32LL * kPanelSMs ? 32 : total_cols >= 1024 ? 16 : 0;
+      if (tcm == 0) tcm = total_cols >= 32LL * kPanelSMs ? 32 : total_cols >= 2048 ? 16 : 0;
       if (tcm == 16 || tcm == 32) {
         if (tile_used) *tile_used = tcm;
         WalkBatch<T, float> Bm;

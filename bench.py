@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the heuristic column tiles (deterministic kernel choice, e.g. for profiling)")
     ap.add_argument("--coarse-direct", type=int, default=-1,
                     help="grid size solved exactly as coarse-grid correction (-1: 255 in 1D, 31 in 2D; "
                          "1: the paper's recursion to one point)")
@@ -84,7 +86,8 @@ def workload(a):
     gamma = (2 - a.alpha) / a.alpha
     return {"workload": f"1D H-matrix, N={a.N}, M={a.M}, alpha={a.alpha}, gamma={gamma:.4g}, leaf 64, tol 1e-10, "
                         f"V(1,1) to relres {a.rtol:g}",
-            "coarse_solve": coarse_desc(coarse_direct(a, 1, a.N)), "tiles": "autotuned (fhmg_problem_autotune)",
+            "coarse_solve": coarse_desc(coarse_direct(a, 1, a.N)),
+            "tiles": "heuristic" if a.no_autotune else "autotuned (fhmg_problem_autotune)",
             "dim": 1, "N": a.N, "M": a.M, "alpha": a.alpha, "gamma": gamma, "leaf": 64, "tol": 1e-10,
             "cycle": "V(1,1)", "rtol": a.rtol, "source": "manufactured t^alpha sin(pi x)",
             "l2": "inputs larger than L2 (u, f 134 MB each)"}
@@ -219,7 +222,7 @@ def timed_solves(P, f, steps, warmup, rtol, stream, dist):
     return {"ms": ms, "cycles": cycles, "relres": rr, "cnt": cnt, "u": u}
 
 
-def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, dist, dev, nc=1):
+def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, dist, dev, nc=1, tune=True):
     import torch
     t0 = time.perf_counter()
     H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
@@ -231,7 +234,8 @@ def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, di
     for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
         P = fh.Problem(H, dim, N, 1.0, prec, stream)
         P.set_coarse_direct(nc)
-        P.autotune()  # column tiles timed per (kind, mode, columns); setup, untimed
+        if tune:
+            P.autotune()  # column tiles timed per (kind, mode, columns); setup, untimed
         r = timed_solves(P, f, steps, warmup, rtol, stream, dist)
         r["P"] = P
         r["time_to_rtol_s"] = r["ms"] / steps / 1e3
@@ -362,7 +366,8 @@ def roofline(H, r, ncols_avg, kind):
         kern = "hpanel_kernel<double,double,64,*,SMOOTH> (finest-grid half-sweep)"
     else:
         peak, note = FP32_PEAK_TFLOPS, "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (an FFMA loop measured 75.1)"
-        kern = "hpanel_kernel<*,float,64,*,SMOOTH> (finest-grid half-sweep, FP32 products)"
+        kern = ("finest-grid half-sweep, FP32 products: hmma_kernel<double,16,SMOOTH> (3xTF32 tensor cores) "
+                "or hpanel_kernel<double,float,64,*,SMOOTH>, per the autotuned tile")
     return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "peak_note": note, "traffic": None, "avg_launch_ms": sm_ms,
             "launches_timed": c["smooth_launches"], "algorithmic_flops_per_launch": flops_launch,
@@ -414,7 +419,7 @@ def main():
 
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     H, f, res, t_hbuild = measure(fh, inputs, 1, a.N, a.M, a.alpha, gamma, a.steps, a.warmup, a.rtol, stream, dist, dev,
-                                  coarse_direct(a, 1, a.N))
+                                  coarse_direct(a, 1, a.N), not a.no_autotune)
     clk = clocks.stop() if clocks else None
 
     k_ref = res["fp64"]["cycles"] / a.steps
@@ -450,7 +455,8 @@ def main():
         N2, M2, al2, ga2 = 511, 1024, 0.4, 2.5
         st2, wu2 = min(a.steps, 2), 1
         nc2 = coarse_direct(a, 2, N2)
-        H2, f2, res2, tb2 = measure(fh, inputs, 2, N2, M2, al2, ga2, st2, wu2, a.rtol, stream, dist, dev, nc2)
+        H2, f2, res2, tb2 = measure(fh, inputs, 2, N2, M2, al2, ga2, st2, wu2, a.rtol, stream, dist, dev, nc2,
+                                    not a.no_autotune)
         k2 = res2["fp64"]["cycles"] / st2
         dof2 = N2 * N2 * M2
         for r in res2.values():
@@ -483,6 +489,12 @@ def main():
     # the headline step's dominant kernel: the FP32-product smoother or the FP64 outer defect
     rl_s = roofline(H, res["mixed"], a.N / 2.0, "mixed")
     rl_d = roofline_defect(H, res["mixed"], a.N, "df")
+    if a.N == 4095 and a.M == 4096 and a.alpha == 0.5:
+        # DRAM bytes per launch from the ncu captures (profiles/), same kernels and workload
+        rl_s["traffic"] = 366.6e6
+        rl_s["traffic_source"] = "profiles/hmma_mixed_smooth_1d_4095x4096.md (ncu dram read+write, one launch)"
+        rl_d["traffic"] = 382.2e6
+        rl_d["traffic_source"] = "profiles/hdf_defect_1d_4095x4096.md (ncu dram read+write, one launch)"
     rl_head = dominant(rl_s, rl_d)
     rl_second = rl_d if rl_head is rl_s else rl_s
     if rank == 0:

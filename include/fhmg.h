@@ -179,11 +179,12 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
  * a warm start with the zero initial guess fairly. */
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
 
-/* Arithmetic of the mixed path's outer defect products (the FP64 residual that judges
- * convergence): 1 (default) double-float -- pairs of floats with error-free transformations on
- * the FP32 pipe (entries and x split as a = hi + lo, |a - hi - lo| <= 2^-48 |a|; each product
- * accurate to a few 2^-48 of sum |a_k x_k|), which on GB300 outruns the 1/64-rate FP64 pipe;
- * 0 FP64 (DFMA).  The stencil part and r = F - ... are FP64 in both. */
+/* Arithmetic of the mixed path's FP64-accurate steps -- the outer defect products (the residual
+ * that judges convergence) and the mode solves of the exactly solved coarse level
+ * (fhmg_problem_set_coarse_direct): 1 (default) double-float -- pairs of floats with error-free
+ * transformations on the FP32 pipe (entries and x split as a = hi + lo, |a - hi - lo| <= 2^-48 |a|;
+ * each dot product accurate to a few 2^-48 of sum |a_k x_k|), which on GB300 outruns the 1/64-rate
+ * FP64 pipe; 0 FP64 (DFMA).  The stencil part and r = F - ... are FP64 in both. */
 int fhmg_problem_set_defect_arith(fhmg_problem p, int mode);
 
 /* FP32 products of the mixed path on the tensor cores (enable != 0, the default): with leaf 64,

@@ -19,10 +19,12 @@ namespace fhmg {
 // (D_ii + lam_k I)^{-1} for every diagonal leaf i of R~ and every mode k, in the layout of the
 // FP64 DIAG chunks: entry (c, r) of a leaf's inverse at ((c / 2) * L + r) * 2 + c % 2.
 // One CTA per (i, k); thread c forward-substitutes (D_ii + lam I) x = e_c (column c).
-// Dd: nb leaf blocks, L x L row-major; out: nmodes x nb x L x L.  Dynamic shared memory:
-// 2 L^2 doubles.
+// Dd: nb leaf blocks, L x L row-major; out: nmodes x nb x L x L.  out_df (optional): the same
+// inverses as float pairs in the layout of the double-float DIAG chunks (hi block: entry (c, r) at
+// ((c / 4) * L + r) * 4 + c % 4; lo block L^2 floats later), nmodes x nb x 2 L^2 floats.
+// Dynamic shared memory: 2 L^2 doubles.
 __global__ void mode_inverse_kernel(const double* __restrict__ Dd, const double* __restrict__ lam, int L, int nb,
-                                    double* __restrict__ out) {
+                                    double* __restrict__ out, float* __restrict__ out_df) {
   extern __shared__ double sh[];
   double* D = sh;          // D_ii, row-major
   double* X = sh + L * L;  // X[r * L + c], the inverse
@@ -45,6 +47,17 @@ __global__ void mode_inverse_kernel(const double* __restrict__ Dd, const double*
     const int g = e / (2 * L), rem = e % (2 * L);
     const int r = rem / 2, col = 2 * g + rem % 2;
     o[e] = X[r * L + col];
+  }
+  if (out_df) {
+    float* od = out_df + ((size_t)k * nb + i) * 2 * L * L;
+    for (int e = c; e < L * L; e += blockDim.x) {
+      const int g = e / (4 * L), rem = e % (4 * L);
+      const int r = rem / 4, col = 4 * g + rem % 4;
+      const double v = X[r * L + col];
+      const float hi = __double2float_rn(v);
+      od[e] = hi;
+      od[L * L + e] = __double2float_rn(v - (double)hi);
+    }
   }
 }
 

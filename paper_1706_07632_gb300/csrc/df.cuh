@@ -1,5 +1,6 @@
-// FP64-accurate H-matrix products (Algorithm 3 per column: OUT = B - R~ X) in double-float
-// arithmetic on the FP32 pipe.  On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, and the
+// FP64-accurate H-matrix products (Algorithm 3 per column: OUT = B - R~ X) and triangular solves
+// on compact columns (Algorithm 4: X = (R~ + s I)^{-1} B, one inverse set per column allowed) in
+// double-float arithmetic on the FP32 pipe.  On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, and the
 // defect that judges convergence must be accurate to FP64 level; a double-float multiply-add
 // (pairs of floats, error-free transformations) costs 11 FP32 instructions instead of one
 // 1/64-rate DFMA.
@@ -10,8 +11,9 @@
 // dropped.  Sums keep (h, l) with TwoSum on h.  The error of a dot product is a few 2^-48 of
 // sum |a_k x_k|; OUT = B - (h + l) is formed in FP64.
 //
-// Walk, chunk stream, producer warp and bounded mbarrier protocol are those of hpanel_kernel in
-// MODE_MATVEC (panel.cuh); x tiles and the z pool are kept as (hi, lo) pairs in shared memory.
+// Walk, chunk stream, producer warp and bounded mbarrier protocol are those of hpanel_kernel
+// (panel.cuh); x tiles, y and the z pool are kept as (hi, lo) pairs in shared memory.  The smoother
+// form streams the inverses (D_ii + s I)^{-1} as float pairs in place of the DIAG chunks.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -54,14 +56,15 @@ __device__ __forceinline__ void df_split(double x, float& h, float& l) {
 }
 
 struct DfSmem {
-  size_t ring, zp, bar, ebar, cbar, desc, flag, total;
+  size_t ysm, ring, zp, bar, ebar, cbar, desc, flag, total;
 };
 // x-tile ring: W slots x {hi, lo} x TC columns x (L + 4) floats; z pool: {hi, lo} x pool x TC
 __host__ __device__ inline DfSmem df_smem(int L, int TC, int pool, int W, int slot_bytes, int ns) {
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   const size_t LP = (size_t)L + 4;
   DfSmem s;
-  s.ring = a16((size_t)ns * slot_bytes);
+  s.ysm = a16((size_t)ns * slot_bytes);  // y of the current leaf (smoother): {hi, lo} x TC x LP
+  s.ring = a16(s.ysm + 2 * (size_t)TC * LP * 4);
   s.zp = a16(s.ring + (size_t)W * 2 * TC * LP * 4);
   s.bar = a16(s.zp + 2 * (size_t)pool * TC * 4);
   s.ebar = s.bar + 8 * (size_t)ns;
@@ -81,7 +84,9 @@ __device__ __forceinline__ void df_vec(float (&h)[4], float (&l)[4], const float
   df_mac(h[3], l[3], ah.w, al.w, xh.w, xl.w);
 }
 
-template <int L, int TC>
+// MODE_SMOOTH: compact columns only (geo.dim == 0, no stencil), B the right-hand side, Dinv the
+// inverses as float pairs (2 L^2 floats per leaf), dinv_cstride floats between columns' sets.
+template <int L, int TC, int MODE>
 __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBatch<double, float> B) {
   constexpr int NT = 256, VE = 4;
   using TL = PTile<L, TC, NT, VE>;
@@ -92,6 +97,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
   const DfSmem lay = df_smem(L, TC, B.pool, B.W, B.slot_bytes, B.ns);
   unsigned char* slots = sm;
   float* ring = reinterpret_cast<float*>(sm + lay.ring);
+  float* ysh = reinterpret_cast<float*>(sm + lay.ysm);
   float* zph = reinterpret_cast<float*>(sm + lay.zp);
   float* zpl = zph + (size_t)B.pool * TC;
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + lay.bar);
@@ -134,8 +140,11 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
           break;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const void* src = (MODE == MODE_SMOOTH && (cd.x & 15) == PK_DIAG)
+                              ? (const void*)(J.Dinv + (g - J.tile0) * TC * J.dinv_cstride + (long long)cd.y * 2 * L * L)
+                              : (const void*)(J.P.pkg + 16LL * (long long)cd.w);
         sdesc[slot] = cd;
-        bulk_load(slots + (size_t)slot * B.slot_bytes, J.P.pkg + 16LL * (long long)cd.w, (uint32_t)cd.z, full + slot);
+        bulk_load(slots + (size_t)slot * B.slot_bytes, src, (uint32_t)cd.z, full + slot);
         if (++slot == ns) slot = 0;
       }
     }
@@ -197,7 +206,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
         if (act && sp == 0 && valid && leaf < nb) {
           const long long base = (long long)(leaf * L + rb + RG * q) * ld + p;
           b = Bsrc[base];
-          x = X[base];
+          if (MODE == MODE_MATVEC) x = X[base];
         }
         bn[q] = b;
         xn[q] = x;
@@ -223,7 +232,61 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
         const int type = cd.x & 15, cnt = (cd.x >> 4) & 0xff;
         const unsigned char* buf = slots + (size_t)cslot * B.slot_bytes;
         const float4* Ah = reinterpret_cast<const float4*>(buf);
-        if (type == PK_DENSE || type == PK_DIAG) {
+        if (MODE == MODE_SMOOTH && type == PK_DIAG) {
+          // y = B - (products so far) in FP64, then x_i = Dinv y in double-float
+          const float4* Al = Ah + L * L / 4;
+          float* yh = ysh + (size_t)cl * LP;
+          float* yl = ysh + (size_t)(TC + cl) * LP;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            float h = ph[q][0], l = pl[q][0];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) df_add(h, l, ph[q][a], pl[q][a]);
+#pragma unroll
+            for (int o = STEP; o < 32; o <<= 1) {
+              const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+              const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+              df_add(h, l, oh, ol);
+            }
+            rhs[q] -= (double)h + (double)l;
+            if (sp == 0 && act) {
+              float a, b2;
+              df_split(rhs[q], a, b2);
+              yh[rb + RG * q] = a;
+              yl[rb + RG * q] = b2;
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) ph[q][a] = pl[q][a] = 0.f;
+          }
+          if (!consumer_sync()) return;  // y is complete
+#pragma unroll
+          for (int gg = 0; gg < NVT; ++gg) {
+            const int g = sp + gg * S;
+            const float4 vh = *reinterpret_cast<const float4*>(yh + g * VE);
+            const float4 vl = *reinterpret_cast<const float4*>(yl + g * VE);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) df_vec(ph[q], pl[q], Ah[g * L + rb + RG * q], Al[g * L + rb + RG * q], vh, vl);
+          }
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            float h = ph[q][0], l = pl[q][0];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) df_add(h, l, ph[q][a], pl[q][a]);
+#pragma unroll
+            for (int o = STEP; o < 32; o <<= 1) {
+              const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+              const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+              df_add(h, l, oh, ol);
+            }
+            if (sp == 0 && act) {
+              tile_h(si)[rb + RG * q] = h;  // (h, l) is already a float pair of x
+              tile_l(si)[rb + RG * q] = l;
+              if (valid) J.X[(long long)(i * L + rb + RG * q) * ld + p] = (double)h + (double)l;
+            }
+          }
+          load_rhs(i + 1);
+          if (!consumer_sync()) return;  // x_i is published for the V slabs
+        } else if (type == PK_DENSE || type == PK_DIAG) {
           const float4* Al = Ah + L * L / 4;
           const float *xh, *xl;
           if (type == PK_DIAG) {
@@ -352,7 +415,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
         }
       }
     }
-    if (J.norm != nullptr) {
+    if (MODE == MODE_MATVEC && J.norm != nullptr) {
       for (int o = 16; o > 0; o >>= 1) {
         const double other = __shfl_xor_sync(0xffffffffu, local_max, o);
         local_max = (other > local_max || other != other) ? other : local_max;

@@ -117,6 +117,7 @@ struct fhmg_problem_s {
   int lcd = -1;                 // its level index (< nlev - 1), -1: none
   double2* dTw = nullptr;       // FFT twiddles exp(-2 pi i j / P), j < P/2, P = 2 (n + 1)
   double* dModeInv = nullptr;   // (D_ii + lam_k I)^{-1}: modes x nb x L x L, DIAG chunk layout
+  float* dModeInvDF = nullptr;  // the same as float pairs (mixed problems: double-float mode solves)
   double* dCA = nullptr;        // scratch, M x points of that level
   double* dCB = nullptr;
   std::vector<void*> dallocs;   // the buffers above
@@ -389,19 +390,21 @@ int direct_level(fhmg_problem p, int l, T* E, const T* RC) {
   }
   ++p->launches;
   CK(cudaGetLastError());
+  // mixed problems: the mode solves in FP64-accurate double-float arithmetic (FP32 pipe)
+  const bool df = p->dModeInvDF && p->defect_df;
   fhmg::WalkArgsT<double> a{};
-  a.P = p->panel64.d;
+  a.P = df ? p->panel64df.d : p->panel64.d;
   a.mode = fhmg::MODE_SMOOTH;
   a.geo = Geo{0, 0, 0, lv.npts, 0.0};  // compact columns, no stencil: X = (R~ + lam I)^{-1} B
   a.ncols = lv.npts;
   a.X = p->dCB;
   a.B = p->dCA;
-  a.Dinv = p->dModeInv;
-  a.dinv_cstride = (long long)p->nb * p->L * p->L;
+  a.Dinv = df ? (const void*)p->dModeInvDF : (const void*)p->dModeInv;
+  a.dinv_cstride = (long long)p->nb * p->L * p->L * (df ? 2 : 1);
   a.err = p->derr;
   a.tile = 1;
   std::vector<fhmg::WalkArgsT<double>> j{a};
-  TRY(launch_jobs(p->st, K64, j, &p->launches));
+  TRY(launch_jobs(p->st, df ? KDF : K64, j, &p->launches));
   if (p->dim == 1) {
     fhmg::sine_fft_kernel<double, T><<<lines_x, thr, smem, p->st>>>(p->dCB, E, p->dTw, M, 1, n, 0, log2P);
   } else {
@@ -1132,6 +1135,7 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   for (void* a : p->dallocs) cudaFree(a);
   p->dallocs.clear();
   p->dModeInv = p->dCA = p->dCB = nullptr;
+  p->dModeInvDF = nullptr;
   p->dTw = nullptr;
   p->ndirect = 1;
   p->lcd = -1;
@@ -1159,11 +1163,13 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   TRY(upload(p->dallocs, tw, &dtw, nullptr));
   p->dTw = reinterpret_cast<double2*>(const_cast<double*>(dtw));
   TRY(dalloc(p->dallocs, &p->dModeInv, (size_t)lv.npts * nb * L * L));
+  if (p->prec == FHMG_MIXED_FP32 && p->panel64df.d.pkg)
+    TRY(dalloc(p->dallocs, &p->dModeInvDF, (size_t)lv.npts * nb * 2 * L * L));
   TRY(dalloc(p->dallocs, &p->dCA, (size_t)lv.npts * p->M));
   TRY(dalloc(p->dallocs, &p->dCB, (size_t)lv.npts * p->M));
   const int smem = 2 * L * L * (int)sizeof(double);
   CK(cudaFuncSetAttribute(fhmg::mode_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  fhmg::mode_inverse_kernel<<<dim3(nb, (unsigned)lv.npts), L, smem, p->st>>>(dDd, dlam, L, nb, p->dModeInv);
+  fhmg::mode_inverse_kernel<<<dim3(nb, (unsigned)lv.npts), L, smem, p->st>>>(dDd, dlam, L, nb, p->dModeInv, p->dModeInvDF);
   ++p->launches;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->st));

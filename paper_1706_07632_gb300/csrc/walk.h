@@ -34,8 +34,10 @@ int walk_launch_dd(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, st
 int walk_launch_df(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 int walk_launch_ff(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std::string* err, int* tile_used);
 
-// FP64-accurate products (MODE_MATVEC) in double-float arithmetic, walk_dfd.cu: the jobs' P is the
-// build_panel_df stream; tile 4, 8 or 16 (0: automatic).
+// FP64-accurate walks in double-float arithmetic, walk_dfd.cu: products (MODE_MATVEC) or line solves
+// on compact columns (MODE_SMOOTH, geo.dim 0; Dinv: inverses as float pairs, 2 L^2 floats per leaf,
+// dinv_cstride floats per column); the jobs' P is the build_panel_df stream; tile 1, 4, 8 or 16
+// (0: automatic; 1 whenever columns have their own inverses).
 int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 
 // Tensor-core walks (FP32 products, leaf 64, TC 16 or 32), walk_mma.cu.  B.ns is chosen here.

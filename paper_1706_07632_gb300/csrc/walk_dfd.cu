@@ -1,5 +1,6 @@
-// Launcher of the double-float defect product (hdf_kernel, df.cuh): FP64 arrays, FP64-accurate
-// H-matrix products in FP32-pair arithmetic.
+// Launcher of the double-float walks (hdf_kernel, df.cuh): FP64 arrays, FP64-accurate H-matrix
+// products (defects) and line solves on compact columns (the exactly solved level's modes) in
+// FP32-pair arithmetic.
 #include <algorithm>
 #include <string>
 
@@ -12,9 +13,9 @@ namespace {
 constexpr int kDfBlock = 256 + 32;
 constexpr size_t kDfSmemMax = 227 * 1024;
 
-template <int L, int TC>
+template <int L, int TC, int MODE>
 int df_launch_t(cudaStream_t st, WalkBatch<double, float>& B, std::string* err) {
-  auto kern = hdf_kernel<L, TC>;
+  auto kern = hdf_kernel<L, TC, MODE>;
   // with more tiles than SMs and a tile that leaves room for two CTAs' registers (TC <= 8), size
   // the ring for two CTAs per SM (16 consumer warps hide the latency of the double-float chains
   // better than a deeper ring: 3.9 vs 5.3 ms for 4095 columns x M = 4096); else the deepest ring
@@ -60,6 +61,7 @@ int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs
     return 2;
   }
   const int L = jobs[0].P.L;
+  const int mode = jobs[0].mode;
   WalkBatch<double, float> B;
   B.njobs = njobs;
   B.pool = 0;
@@ -68,8 +70,8 @@ int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs
   B.err = jobs[0].err;
   long long cols = 0;
   for (int j = 0; j < njobs; ++j) {
-    if (jobs[j].P.L != L || jobs[j].mode != MODE_MATVEC) {
-      *err = "double-float walk: product jobs of one leaf size only";
+    if (jobs[j].P.L != L || jobs[j].mode != mode || (mode == MODE_SMOOTH && jobs[j].geo.dim != 0)) {
+      *err = "double-float walk: jobs of one leaf size and mode; solves on compact columns only";
       return 2;
     }
     B.pool = std::max(B.pool, jobs[j].P.pool);
@@ -79,7 +81,10 @@ int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs
   }
   // column tile: 8 once the columns give every SM a tile of 8 (two CTAs per SM), else 4
   int TC = jobs[0].tile;
-  if (TC != 4 && TC != 8 && TC != 16) TC = cols >= 8LL * 152 ? 8 : 4;
+  if (TC != 1 && TC != 4 && TC != 8 && TC != 16) TC = cols >= 8LL * 152 ? 8 : cols >= 4LL * 152 ? 4 : 1;
+  bool per_column = false;
+  for (int j = 0; j < njobs; ++j) per_column |= jobs[j].dinv_cstride != 0;
+  if (per_column) TC = 1;  // each column streams its own inverses
   if (tile_used) *tile_used = TC;
   long long tiles = 0;
   for (int j = 0; j < njobs; ++j) {
@@ -91,17 +96,20 @@ int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs
     J.X = jobs[j].X;
     J.B = jobs[j].B;
     J.OUT = jobs[j].OUT;
-    J.Dinv = nullptr;
-    J.dinv_cstride = 0;
+    J.Dinv = (const float*)jobs[j].Dinv;
+    J.dinv_cstride = jobs[j].dinv_cstride;
     J.ddiag = nullptr;
     J.norm = jobs[j].norm;
     tiles += (jobs[j].ncols + TC - 1) / TC;
   }
   B.ntiles = tiles;
   B.ns = 2;
-#define FHMG_DF(LL, TT) \
-  if (L == LL && TC == TT) return df_launch_t<LL, TT>(st, B, err);
-  FHMG_DF(64, 4) FHMG_DF(64, 8) FHMG_DF(64, 16) FHMG_DF(32, 4) FHMG_DF(32, 8) FHMG_DF(32, 16)
+#define FHMG_DF(LL, TT)                                                                              \
+  if (L == LL && TC == TT)                                                                             \
+    return mode == MODE_SMOOTH ? df_launch_t<LL, TT, MODE_SMOOTH>(st, B, err)                          \
+                               : df_launch_t<LL, TT, MODE_MATVEC>(st, B, err);
+  FHMG_DF(64, 1) FHMG_DF(64, 4) FHMG_DF(64, 8) FHMG_DF(64, 16)
+  FHMG_DF(32, 1) FHMG_DF(32, 4) FHMG_DF(32, 8) FHMG_DF(32, 16)
 #undef FHMG_DF
   *err = "no double-float walk for leaf " + std::to_string(L);
   return 2;

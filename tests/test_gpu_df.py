@@ -87,8 +87,8 @@ def test_df_needs_a_mixed_problem():
 
 
 def test_mixed_solve_same_with_fp64_and_double_float_defects():
-    """1D N=4095, M=4096: the mixed solve takes the same cycles with either defect arithmetic and
-    both solutions match the per-mode oracle to 1e-7."""
+    """1D N=4095, M=4096: the mixed solve takes the same cycles with either arithmetic for the outer
+    defect and the coarse mode solves, and both solutions match the per-mode oracle to 1e-7."""
     alpha, gamma, M, N = 0.5, 3.0, 4096, 4095
     t = l1.graded_mesh(1.0, M, gamma)
     R = l1.l1_matrix(t, alpha)
@@ -109,6 +109,29 @@ def test_mixed_solve_same_with_fp64_and_double_float_defects():
         err = float((u - ref).abs().max() / ref.abs().max())
         assert rr <= 1e-8 and err < 1e-7, (arith, k, rr, err)
         out.append((k, rr, u))
+    # arithmetic 1 also runs the exactly solved level's mode solves in double-float: the coarse
+    # corrections then differ at the 1e-13 level and the FP32-product inner cycles carry that into
+    # the iterates, so the two solutions agree to the solve's tolerance, not bit for bit
     assert out[0][0] == out[1][0]
-    assert abs(out[0][1] - out[1][1]) <= 1e-3 * out[0][1]
-    assert float((out[0][2] - out[1][2]).abs().max() / ref.abs().max()) < 1e-12
+    assert abs(out[0][1] - out[1][1]) <= 0.5 * out[0][1]
+    assert float((out[0][2] - out[1][2]).abs().max() / ref.abs().max()) < 1e-9
+
+
+@pytest.mark.parametrize("dim,N,nc", [(1, 127, 31), (2, 31, 7)])
+def test_vcycle_with_double_float_mode_solves(dim, N, nc):
+    """A mixed-precision problem's FP64 V-cycle (fhmg_vcycle) solves the exact coarse level's modes in
+    double-float arithmetic: one cycle against the oracle's cycle with the same coarse correction."""
+    from oracle import wrmg
+    alpha, gamma, M = 0.5, 2.0, 256
+    t = l1.graded_mesh(1.0, M, gamma)
+    R = l1.l1_matrix(t, alpha)
+    H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 0.0)
+    P = fh.Problem(H, dim, N, prec=fh.MIXED_FP32)
+    P.set_coarse_direct(nc)
+    shape = (M, N) if dim == 1 else (M, N, N)
+    u0 = inputs.random_field(42, shape)
+    F = inputs.random_field(43, shape) * 10
+    u = dev(u0)
+    P.vcycle(u, dev(F), None, 1, 1)
+    ref = wrmg.cycle(R, F, u0, 1.0 / (N + 1), 1, 1, n_direct=nc)
+    assert rel(host(u), ref) < 1e-11

@@ -135,15 +135,38 @@ class Clocks:
 
 
 def dist_setup():
+    """Rank, world size and the process group of a torchrun launch (replicas only: the group is
+    used for the barrier and the max-over-ranks timing, never on the data path).  NCCL between
+    GPUs; gloo when no GPU is visible (host-only runs of the multi-process tests).  Idempotent."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            if torch.cuda.is_available():
+                torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+                dist.init_process_group("nccl")
+            else:
+                dist.init_process_group("gloo")
         return dist, rank, ws
     return None, 0, 1
+
+
+def max_over_ranks(x, dist):
+    """The largest value of x over all ranks (the timing rule: the slowest rank sets the time)."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_value(units_per_rank, ranks, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * ranks / seconds
 
 
 def oracle_direct_sample(a):
@@ -215,10 +238,7 @@ def timed_solves(P, f, steps, warmup, rtol, stream, dist):
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    if dist:
-        mx = torch.tensor([ms], device=f.device)
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        ms = float(mx[0])
+    ms = max_over_ranks(ms, dist)
     return {"ms": ms, "cycles": cycles, "relres": rr, "cnt": cnt, "u": u}
 
 
@@ -424,7 +444,7 @@ def main():
 
     k_ref = res["fp64"]["cycles"] / a.steps
     for r in res.values():
-        r["value"] = dof * k_ref * ws / r["time_to_rtol_s"]
+        r["value"] = job_value(dof * k_ref, ws, r["time_to_rtol_s"])
     head = res["mixed"]
 
     e2e = None
@@ -439,7 +459,8 @@ def main():
             uh.zero_()
             P.solve_host(uh, fh_host, None, 1, 1, a.rtol, 80)
         te = time.perf_counter() - t0
-        e2e = {"value": dof * k_ref * ws * a.steps / te, "unit": "DOF*cycles/s", "h2d_bytes_per_step": 2 * dof * 8,
+        te = max_over_ranks(te, dist)
+        e2e = {"value": job_value(dof * k_ref * a.steps, ws, te), "unit": "DOF*cycles/s", "h2d_bytes_per_step": 2 * dof * 8,
                "d2h_bytes_per_step": dof * 8, "ms_per_step": 1e3 * te / a.steps}
         del fh_host, uh
 
@@ -460,7 +481,7 @@ def main():
         k2 = res2["fp64"]["cycles"] / st2
         dof2 = N2 * N2 * M2
         for r in res2.values():
-            r["value"] = dof2 * k2 * ws / r["time_to_rtol_s"]
+            r["value"] = job_value(dof2 * k2, ws, r["time_to_rtol_s"])
         w2d = {"workload": f"2D H-matrix, N={N2}^2, M={M2}, alpha={al2}, gamma={ga2}, leaf 64, tol 1e-10, V(1,1) to "
                            f"relres {a.rtol:g}", "coarse_solve": coarse_desc(nc2),
                "fp64": summary(res2["fp64"], st2), "mixed": summary(res2["mixed"], st2),

@@ -180,7 +180,7 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
 
 /* Arithmetic of the mixed path's FP64-accurate steps -- the outer defect products (the residual
- * that judges convergence) and the mode solves of the exactly solved coarse level
+ * that decides convergence) and the mode solves of the exactly solved coarse level
  * (fhmg_problem_set_coarse_direct): 1 (default) double-float -- pairs of floats with error-free
  * transformations on the FP32 pipe (entries and x split as a = hi + lo, |a - hi - lo| <= 2^-48 |a|;
  * each dot product accurate to a few 2^-48 of sum |a_k x_k|), which on GB300 outruns the 1/64-rate

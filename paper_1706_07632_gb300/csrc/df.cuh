@@ -1,7 +1,7 @@
 // FP64-accurate H-matrix products (Algorithm 3 per column: OUT = B - R~ X) and triangular solves
 // on compact columns (Algorithm 4: X = (R~ + s I)^{-1} B, one inverse set per column allowed) in
 // double-float arithmetic on the FP32 pipe.  On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, and the
-// defect that judges convergence must be accurate to FP64 level; a double-float multiply-add
+// defect that decides convergence must be accurate to FP64 level; a double-float multiply-add
 // (pairs of floats, error-free transformations) costs 11 FP32 instructions instead of one
 // 1/64-rate DFMA.
 //

@@ -5,8 +5,8 @@
 // time discretisation: u = sum_pq c_pq w_pq(t) s_pq with (R + lam_pq I) w_pq = 1.  The network
 // predicts y = lam * w(t) in [0, 1) from features of (lam, alpha, t); the warm start projects f
 // onto the K x K leading modes, evaluates the network for every (mode, time level) and
-// synthesises u0 = sum_pq c_pq w_pq(t_m) s_pq.  Multigrid then solves from u0 and is the judge of
-// its error (and the fallback: u0 = 0).
+// synthesises u0 = sum_pq c_pq w_pq(t_m) s_pq.  Multigrid then solves from u0 and measures
+// its error (and is the fallback: u0 = 0).
 //
 // Network: F = 6 input features -> H -> H -> H -> 1, SiLU activations, FP32 training (Adam), FP32
 // or BF16 inference.  Layer l maps width n_l to n_{l+1} with weights W_l (n_{l+1} x n_l,

@@ -95,5 +95,5 @@ def test_trained_warm_start_saves_cycles():
     uw = net.predict(P, f, alpha, K=24, bf16=True)
     kw, _ = P.solve(uw, f, None, 1, 1, 1e-8, 40)
     assert kw < k0, (kw, k0)
-    # multigrid judges the warm start: both iterates meet the same absolute defect target
+    # multigrid decides on the warm start: both iterates meet the same absolute defect target
     assert float((uw - u0).abs().max() / u0.abs().max()) < 1e-6

@@ -7,6 +7,22 @@
 
 namespace fhmg {
 
+// Raises kern's dynamic shared-memory limit to smem on the current device.  The attribute is held
+// per device, so the limit already set is remembered per device (configured: one entry per device).
+constexpr int kDevSlots = 64;
+template <typename K>
+inline cudaError_t raise_smem_limit(K kern, size_t smem, size_t (&configured)[kDevSlots]) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  size_t& c = configured[dev % kDevSlots];
+  if (smem <= c) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) c = smem;
+  return e;
+}
+
 // One walk job (one instance).
 template <typename T>
 struct WalkArgsT {

@@ -31,14 +31,13 @@ int df_launch_t(cudaStream_t st, WalkBatch<double, float>& B, std::string* err) 
   }
   B.ns = ns;
   const size_t smem = df_smem(L, TC, B.pool, B.W, B.slot_bytes, ns).total;
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static size_t configured[kDevSlots] = {};
+  {
+    cudaError_t e = raise_smem_limit(kern, smem, configured);
     if (e != cudaSuccess) {
       *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
       return 1;
     }
-    configured = smem;
   }
   int occ = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDfBlock, smem) != cudaSuccess || occ < 1) occ = 1;

@@ -27,16 +27,15 @@ template <typename T, typename TM, int L, int TC, int MODE>
 int panel_launch_t(cudaStream_t st, const WalkBatch<T, TM>& B, std::string* err) {
   auto kern = hpanel_kernel<T, TM, L, TC, MODE, kPanelThreads>;
   const size_t smem = panel_bytes<T, TM>(L, TC, B.pool, B.W, B.slot_bytes, B.ns);
-  static size_t configured = 48 * 1024;
+  static size_t configured[kDevSlots] = {};
   static size_t occ_smem = 0;
   static int occ = 1;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = raise_smem_limit(kern, smem, configured);
     if (e != cudaSuccess) {
       *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
       return 1;
     }
-    configured = smem;
   }
   if (occ_smem != smem) {
     int o = 0;

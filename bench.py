@@ -1,31 +1,37 @@
-"""Benchmark: space-time DOF * cycles / s (time-to-1e-8 solve) of multigrid waveform relaxation.
+"""Benchmark: time-to-1e-8 solves of multigrid waveform relaxation for the time-fractional heat
+equation, mixed precision + learned warm start against plain FP64, on one GB300.
 
-Headline workload: 1D time-fractional heat equation, N = 4095 interior points, M = 4096 graded time
-steps, alpha = 0.5, gamma = (2 - alpha)/alpha = 3, H-matrix leaf 64 with recompression tolerance
-1e-10, manufactured u = t^alpha sin(pi x), zero initial guess, V(1,1) cycles until the max-norm
-residual drops by 1e-8.  One step = one complete solve: every hot-path kernel (smoother
-half-sweeps, defect + restriction, prolongation, coarsest solve, defect norms) runs inside it.
-Also measured (key "workload_2d"): the 2D workload N = 511^2, M = 1024, alpha = 0.4, gamma = 2.5.
-Coarse-grid correction: the 255-point level (1D) / 31^2 level (2D) is solved exactly in FP64 (sine
-transform in space, one H-matrix triangular walk per spatial mode); --coarse-direct 1 runs the
-paper's recursion to one point instead.
+Headline workload (the learned-warm-start configuration): 2D unit square, N = 1023^2 interior
+points, M = 512 graded time steps (gamma = 2), alpha = 0.55, H-matrix leaf 64 with recompression
+tolerance 1e-10, source = a Gaussian random field (length scale 0.1) drawn as a 2D sine series,
+constant in time; V(1,1) cycles until the max-norm defect is <= 1e-8 max|F| (the same absolute
+target for every initial guess); the coarse-grid correction on the 31^2 level is solved exactly.
+One step = one complete warm-started solve: the network's prediction of the initial iterate
+(projection, BF16 inference, synthesis) and the mixed-precision solve from it (defect correction:
+FP64-accurate double-float outer defects around V-cycles with FP32 storage and 3xTF32
+tensor-core H-matrix products).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-2d]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
 
-value     = DOF * K_ref * ranks / (device time per solve), K_ref = the FP64 V(1,1) cycle count of
-            the workload (8 for the headline), so every arm and path is compared on
-            time-to-solution in one unit.  value is the mixed-precision path (defect correction,
-            FP32 H-matrix products inside the cycles, an FP64-accurate outer defect whose products
-            run in double-float arithmetic); the FP64 path is reported beside it.
-e2e       = the same metric through fhmg_solve_host (pinned host buffers; H2D of u and f and D2H
-            of u inside the timed region).
-roofline  = the dominant kernel of the headline step -- the finest-grid smoother half-sweeps or the
-            outer defect, whichever has the larger share -- timed live with CUDA events on the
-            launching stream inside the timed solves (the other one: roofline_secondary).
-cpu_baseline / --impl reference = the oracle's direct solve (implicit time stepping with the dense
-            L1 history sum, numpy/OpenBLAS) of the same workload on the host cores.
+value     = DOF * K_ref * ranks / (device time per step), DOF = N^2 M, K_ref = the FP64 path's V(1,1)
+            cycle count on the headline source: every arm is expressed in FP64-cycle equivalents,
+            so values compare time to solution.  Arms beside it: plain FP64 from zero and mixed
+            from zero, each the median of >= 5 timed solves; err_vs_oracle of every arm at 4096
+            sampled grid points against the per-mode oracle.
+sources   = 16 unseen GRF sources with alpha ~ U[.3, .8]: cycles and time from zero and from the
+            warm start, and the error against the per-mode oracle, per source.
+e2e       = the same metric through fhmg_ws_solve_host (pinned host buffers: f in, u out, inside
+            the timed region).
+roofline  = the dominant kernel of the headline step (the finest-grid smoother half-sweeps or the
+            outer defect, whichever takes the larger share), timed live with CUDA events on the
+            launching stream inside the timed steps; the other one: roofline_secondary.
+cpu_baseline / --impl reference = the oracle's direct solver (implicit time stepping with the dense
+            L1 history sum and a DST-I spatial solve per step, numpy/scipy) on the host cores, on the
+            first time levels of the headline workload (a bounded sample).
+Secondary workloads (keys workload_1d, workload_2d, workload_batched): 1D N=4095, M=4096,
+alpha=0.5; 2D N=511^2, M=1024, alpha=0.4; 64 batched 1D instances.
 N > 1 (torchrun): replicas only -- each rank solves its own instance; no data-path collective.
-Inputs (u, f: 134 MB each in 1D, 2.1 GB in 2D) exceed the 129 MB L2.
+Inputs (u, f: 4.3 GB each) exceed the 129 MB L2.
 """
 from __future__ import annotations
 
@@ -47,54 +53,38 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: FFMA units x clock (a
 # double-float multiply-add = 11 FP32 instructions (TwoProd by FMA, two cross-term FMAs, TwoSum,
 # low-word update): 2 algorithmic flops per 11 FP32 lane-instructions
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / 11 / 1e12  # 7.32
-REF_CYCLES_1D = 8   # FP64 V(1,1) cycles to 1e-8 on the headline workload, measured on GB300
+HEAD = dict(dim=2, N=1023, M=512, alpha=0.55, gamma=2.0, seed=999, K=24, nc=31)
+METRIC = "space-time DOF*cycles/s (time-to-1e-8 solve): mixed+warm-start vs plain FP64"
+# DRAM bytes per column of one launch, from the ncu captures named beside each (same kernels and
+# tiles on the 2D 255^2 x 512 case, scaled by columns); None where no capture of the current kernel
+TRAFFIC_PER_COLUMN = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--alpha", type=float, default=0.5)
-    ap.add_argument("--N", type=int, default=4095)
-    ap.add_argument("--M", type=int, default=4096)
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--sources", type=int, default=16, help="unseen GRF sources of the warm-start sweep")
+    ap.add_argument("--quick", action="store_true", help="headline only (no sweep, secondary workloads, CPU baseline)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the heuristic column tiles (deterministic kernel choice, e.g. for profiling)")
-    ap.add_argument("--coarse-direct", type=int, default=-1,
-                    help="grid size solved exactly as coarse-grid correction (-1: 255 in 1D, 31 in 2D; "
-                         "1: the paper's recursion to one point)")
     return ap.parse_args()
 
 
-def coarse_direct(a, dim, N):
-    """Coarse level solved exactly (FP64 sine transform + one H-matrix walk per mode)."""
-    n = a.coarse_direct if a.coarse_direct >= 0 else (255 if dim == 1 else 31)
-    return n if 1 < n < N else 1
-
-
-def coarse_desc(n):
-    return ("recursion to one point (the paper's cycle)" if n <= 1 else
-            f"exact FP64 solve on the {n}-point level (DST-I in space, one H-matrix walk per mode)")
-
-
-def workload(a):
-    gamma = (2 - a.alpha) / a.alpha
-    return {"workload": f"1D H-matrix, N={a.N}, M={a.M}, alpha={a.alpha}, gamma={gamma:.4g}, leaf 64, tol 1e-10, "
-                        f"V(1,1) to relres {a.rtol:g}",
-            "coarse_solve": coarse_desc(coarse_direct(a, 1, a.N)),
-            "tiles": "heuristic" if a.no_autotune else "autotuned (fhmg_problem_autotune)",
-            "dim": 1, "N": a.N, "M": a.M, "alpha": a.alpha, "gamma": gamma, "leaf": 64, "tol": 1e-10,
-            "cycle": "V(1,1)", "rtol": a.rtol, "source": "manufactured t^alpha sin(pi x)",
-            "l2": "inputs larger than L2 (u, f 134 MB each)"}
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "fallback"
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed work."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -131,7 +121,8 @@ class Clocks:
                     reasons.add(nm)
         os.unlink(self.file.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "span": "every workload of the run (headline, sweep, secondary workloads)"}
 
 
 def dist_setup():
@@ -169,22 +160,71 @@ def job_value(units_per_rank, ranks, seconds):
     return units_per_rank * ranks / seconds
 
 
-def oracle_direct_sample(a):
-    """Times the oracle's direct solve of the full headline workload (dense R history, O1)."""
+def head_config(rtol, tuned=True):
+    h = HEAD
+    return {"workload": (f"2D N={h['N']}^2, M={h['M']}, alpha={h['alpha']}, gamma={h['gamma']}, GRF source "
+                         f"(length scale 0.1, seed {h['seed']}), H-matrix leaf 64 tol 1e-10, V(1,1) to "
+                         f"max|r| <= {rtol:g} max|F|; mixed precision + learned warm start vs plain FP64"),
+            "dim": 2, "N": h["N"], "M": h["M"], "alpha": h["alpha"], "gamma": h["gamma"], "leaf": 64, "tol": 1e-10,
+            "cycle": "V(1,1)", "rtol": rtol, "rtol_reference": "max|F|",
+            "coarse_solve": f"exact solve of the {h['nc']}^2 level (DST-I in space, one H-matrix walk per mode)",
+            "tiles": "autotuned (fhmg_problem_autotune)" if tuned else "heuristic",
+            "warm_start": f"spectral MLP 6->320->320->320->1 (SiLU), BF16 inference, K={h['K']} modes per dimension",
+            "l2": "inputs larger than L2 (u, f 4.3 GB each)"}
+
+
+# ------------------------------------------------------------------ oracle (timing + error checks)
+
+def oracle_R(alpha, gamma, M, cache={}):
+    from oracle import l1
+    key = (alpha, gamma, M)
+    if key not in cache:
+        t = l1.graded_mesh(1.0, M, gamma)
+        cache[key] = (t, l1.l1_matrix(t, alpha))
+    return cache[key]
+
+
+def grf_oracle_at(alpha, gamma, M, N, seed, iy, ix):
+    """Per-mode oracle of a GRF source at sampled grid points (every time level)."""
     import numpy as np
-    from oracle import direct, l1
+    from oracle import direct
     from paper_1706_07632_gb300 import inputs
-    gamma = (2 - a.alpha) / a.alpha
+    t, R = oracle_R(alpha, gamma, M)
+    _, _, c = inputs.grf_2d(seed, t[1:], N)
+    kmax = c.shape[0]
+    lam = direct.laplacian_eigs_1d(N, 1.0 / (N + 1))[:kmax]
+    x = inputs.grid(N)
+    W = np.zeros((M, len(iy)))
+    for p in range(kmax):
+        sy = np.sin((p + 1) * math.pi * x[iy])
+        for q in range(kmax):
+            if c[p, q] != 0.0:
+                w = direct.solve_o2_mode(R, lam[p] + lam[q], np.full(M, c[p, q]))
+                W += np.outer(w, sy * np.sin((q + 1) * math.pi * x[ix]))
+    return W
+
+
+def sampled_err(u, ref, iy, ix):
+    import numpy as np
+    import torch
+    got = u[:, torch.as_tensor(iy, device=u.device), torch.as_tensor(ix, device=u.device)].cpu().numpy()
+    return float(np.abs(got - ref).max() / np.abs(ref).max())
+
+
+def oracle_direct_c5_sample(m_stop):
+    """The oracle's direct solver (O1) on the first m_stop time levels of the headline workload;
+    returns (seconds, DOF processed)."""
+    import numpy as np
+    from oracle import direct
+    from paper_1706_07632_gb300 import inputs
+    h = HEAD
+    t, R = oracle_R(h["alpha"], h["gamma"], h["M"])
+    a, s, _ = inputs.grf_2d(h["seed"], t[1:], h["N"])
+    F = np.empty((m_stop, h["N"], h["N"]))
+    F[:] = s[None]
     t0 = time.perf_counter()
-    t = l1.graded_mesh(1.0, a.M, gamma)
-    R = l1.l1_matrix(t, a.alpha)
-    t_build = time.perf_counter() - t0
-    amp, s = inputs.manufactured(t[1:], a.N, 1, a.alpha)
-    F = np.outer(amp, s)
-    t0 = time.perf_counter()
-    direct.solve_o1(R, F, 1.0 / (a.N + 1))
-    t_solve = time.perf_counter() - t0
-    return t_solve, t_build
+    direct.solve_o1(R[:m_stop, :m_stop], F, 1.0 / (h["N"] + 1))
+    return time.perf_counter() - t0, h["N"] ** 2 * m_stop
 
 
 def run_reference(a):
@@ -192,148 +232,269 @@ def run_reference(a):
     dist, rank, ws = dist_setup()
     if rank != 0:
         return
-    cyc = int(os.environ.get("FHMG_REF_CYCLES", str(REF_CYCLES_1D)))
-    dof = a.N * a.M
+    k_ref = int(os.environ.get("FHMG_REF_CYCLES", "7"))  # FP64 V(1,1) cycles of the headline (GB300 run)
+    m_stop = 48
+    oracle_R(HEAD["alpha"], HEAD["gamma"], HEAD["M"])   # R is set-up, not timed
     for _ in range(max(0, min(a.warmup, 1))):
-        oracle_direct_sample(a)
-    times = [oracle_direct_sample(a)[0] for _ in range(a.steps)]
-    tot = sum(times)
-    value = dof * cyc * a.steps / tot
-    sample = (f"full direct solve N={a.N} M={a.M} per step (implicit time stepping, dense L1 history, numpy/OpenBLAS "
-              f"on all host threads); DOF*cycles with the FP64 cycle count {cyc}")
-    line = {"impl": "reference", "metric": "space-time DOF*cycles/s (time-to-1e-8 solve)", "value": value,
-            "unit": "DOF*cycles/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": workload(a),
+        oracle_direct_c5_sample(m_stop)
+    samples = [oracle_direct_c5_sample(m_stop) for _ in range(a.steps)]
+    tot = sum(s for s, _ in samples)
+    dof = samples[0][1]
+    value = dof * k_ref * a.steps / tot
+    sample = (f"direct solve (implicit time stepping, dense L1 history sum, DST-I spatial solve per step; numpy/scipy "
+              f"on the host threads) of the first {m_stop} of {HEAD['M']} time levels of the headline workload per step; "
+              f"DOF*cycles with the FP64 cycle count {k_ref}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF*cycles/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": head_config(a.rtol),
             "cpu_baseline": {"value": value, "unit": "DOF*cycles/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "DOF*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def timed_solves(P, f, steps, warmup, rtol, stream, dist):
-    """warmup untimed + steps timed solves from u = 0; CUDA events on the launching stream."""
+# ------------------------------------------------------------------ GPU measurements
+
+def events():
     import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def train_net(fh, stream):
+    """The warm-start network, trained on library solves (N=255^2, M=512, 8 alphas, sources with
+    seeds 200..207 -- none of them used below)."""
+    import torch
+    from paper_1706_07632_gb300 import warmstart
+    alphas = [0.3, 0.37, 0.44, 0.51, 0.58, 0.65, 0.72, 0.8]
+    t0 = time.perf_counter()
+    X, Y = warmstart.generate(2, 255, HEAD["M"], HEAD["gamma"], alphas, seeds=list(range(200, 208)), K=HEAD["K"])
+    t_data = time.perf_counter() - t0
+    net = fh.WSNet(320, 3, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = warmstart.train(net, X, Y, steps=3000, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    return net, {"samples": int(X.shape[0]), "data_s": t_data, "train_s": time.perf_counter() - t0,
+                 "loss": losses[-1], "params": net.num_params(), "train_grid": "N=255^2, M=512, 8 alphas, seeds 200-207"}
+
+
+def problem(fh, H, prec, stream, tune):
+    P = fh.Problem(H, 2, HEAD["N"], 1.0, prec, stream)
+    P.set_coarse_direct(HEAD["nc"])
+    P.set_rtol_reference(1)
+    if tune:
+        P.autotune()
+    return P
+
+
+def timed(fn, stream, n):
+    """n calls of fn, each bracketed by CUDA events on the launching stream; returns the times (s)
+    and the last result."""
+    import torch
+    ts, out = [], None
+    for _ in range(n):
+        e0, e1 = events()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return ts, out
+
+
+def measure_headline(fh, a, stream, dist):
+    import numpy as np
+    import torch
+    from paper_1706_07632_gb300 import warmstart
+    h = HEAD
+    net, training = train_net(fh, stream)
+    t0 = time.perf_counter()
+    H = fh.HMatrix(h["alpha"], h["gamma"], 1.0, h["M"], 64, 0, 1e-10)
+    t_hbuild = time.perf_counter() - t0
+    t, _ = H.mesh()
+    f = warmstart.source_field(2, h["seed"], t[1:], h["N"])
+    Pm = problem(fh, H, fh.MIXED_FP32, stream, not a.no_autotune)
     u = torch.zeros_like(f)
-    for _ in range(warmup):
-        u.zero_()
-        P.solve(u, f, None, 1, 1, rtol, 80)
+    rtol = a.rtol
+
+    def warm_step():
+        net.predict(Pm, f, h["alpha"], K=h["K"], bf16=True, u0=u)
+        return Pm.solve(u, f, None, 1, 1, rtol, 60)
+
+    for _ in range(a.warmup):
+        warm_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    P.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cycles, rr = 0, None
+    Pm.profile(True)
+    l0 = fh.wsnet_launches()
+    e0, e1 = events()
     e0.record(stream)
-    for _ in range(steps):
-        u.zero_()
-        k, rr = P.solve(u, f, None, 1, 1, rtol, 80)
-        cycles += k
+    k_warm = 0
+    for _ in range(a.steps):
+        k_warm, rr_warm = warm_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    cnt = P.counters()
-    cnt.update(P.defect_timing())
-    P.profile(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    cnt = Pm.counters()
+    cnt.update(Pm.defect_timing())
+    nn_launches = fh.wsnet_launches() - l0
+    Pm.profile(False)
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(ms, dist)
-    return {"ms": ms, "cycles": cycles, "relres": rr, "cnt": cnt, "u": u}
-
-
-def measure(fh, inputs, dim, N, M, alpha, gamma, steps, warmup, rtol, stream, dist, dev, nc=1, tune=True):
-    import torch
+    rng = np.random.default_rng(77)
+    iy, ix = rng.integers(0, h["N"], 4096), rng.integers(0, h["N"], 4096)
+    ref = grf_oracle_at(h["alpha"], h["gamma"], h["M"], h["N"], h["seed"], iy, ix)
+    arms = {"mixed_warm": {"time_to_rtol_s": ms / a.steps / 1e3, "cycles": k_warm, "relres_vs_maxF": rr_warm,
+                           "err_vs_oracle": sampled_err(u, ref, iy, ix), "steps_timed": a.steps}}
+    arms["mixed_warm"]["predict_s"] = statistics.median(
+        timed(lambda: net.predict(Pm, f, h["alpha"], K=h["K"], bf16=True, u0=u), stream, 3)[0])
+    # mixed from zero: median of 5 solves
+    def zero_solve(P):
+        u.zero_()
+        return P.solve(u, f, None, 1, 1, rtol, 60)
+    zero_solve(Pm)
+    ts, (k, rr) = timed(lambda: zero_solve(Pm), stream, 5)
+    arms["mixed_zero"] = {"time_to_rtol_s": statistics.median(ts), "times_s": ts, "cycles": k, "relres_vs_maxF": rr,
+                          "err_vs_oracle": sampled_err(u, ref, iy, ix)}
+    # e2e: the warm-started solve from pinned host buffers through fhmg_ws_solve_host
+    f_host = f.cpu().pin_memory()
+    u_host = torch.empty(f.shape, dtype=torch.float64).pin_memory()
+    net.solve_host(Pm, u_host, f_host, h["alpha"], h["K"], True, 1, 1, rtol, 60)
+    n_e2e = min(a.steps, 5)
     t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        net.solve_host(Pm, u_host, f_host, h["alpha"], h["K"], True, 1, 1, rtol, 60)
+    te = max_over_ranks(time.perf_counter() - t0, dist)
+    del f_host, u_host
+    del Pm
+    torch.cuda.empty_cache()
+    # plain FP64 from zero: median of 5 solves (heuristic tiles: autotuning the FP64 walks on this
+    # grid takes minutes)
+    Pd = problem(fh, H, fh.FP64, stream, False)
+    zero_solve(Pd)
+    ts, (k, rr) = timed(lambda: zero_solve(Pd), stream, 5)
+    arms["fp64_zero"] = {"time_to_rtol_s": statistics.median(ts), "times_s": ts, "cycles": k, "relres_vs_maxF": rr,
+                         "err_vs_oracle": sampled_err(u, ref, iy, ix)}
+    del Pd
+    torch.cuda.empty_cache()
+    return {"H": H, "arms": arms, "cnt": cnt, "ms": ms, "nn_launches": nn_launches, "training": training,
+            "hbuild_s": t_hbuild, "e2e_s": te / n_e2e, "dof": h["N"] ** 2 * h["M"], "nbytes": f.numel() * 8}
+
+
+def measure_sources(fh, net_holder, a, stream):
+    """Unseen GRF sources, alpha ~ U[.3, .8]: cycles and time from zero and from the warm start."""
+    import numpy as np
+    import torch
+    from paper_1706_07632_gb300 import warmstart
+    h = HEAD
+    net = net_holder
+    rng = np.random.default_rng(4242)
+    rows = []
+    for i in range(a.sources):
+        alpha = float(rng.uniform(0.3, 0.8))
+        seed = 1000 + i
+        H = fh.HMatrix(alpha, h["gamma"], 1.0, h["M"], 64, 0, 1e-10)
+        t, _ = H.mesh()
+        f = warmstart.source_field(2, seed, t[1:], h["N"])
+        P = problem(fh, H, fh.MIXED_FP32, stream, False)
+        u = torch.zeros_like(f)
+
+        def zero():
+            u.zero_()
+            return P.solve(u, f, None, 1, 1, a.rtol, 60)
+
+        def warm():
+            net.predict(P, f, alpha, K=h["K"], bf16=True, u0=u)
+            return P.solve(u, f, None, 1, 1, a.rtol, 60)
+
+        (tz,), (kz, _) = timed(zero, stream, 1)
+        (tw,), (kw, rw) = timed(warm, stream, 1)
+        r = {"alpha": alpha, "seed": seed, "cycles_zero": kz, "cycles_warm": kw, "time_zero_s": tz, "time_warm_s": tw}
+        if i < 4:  # error of the warm-started solution against the per-mode oracle (sampled points)
+            prs = np.random.default_rng(seed)
+            iy, ix = prs.integers(0, h["N"], 1024), prs.integers(0, h["N"], 1024)
+            r["err_vs_oracle"] = sampled_err(u, grf_oracle_at(alpha, h["gamma"], h["M"], h["N"], seed, iy, ix), iy, ix)
+        rows.append(r)
+        del P, H, f, u
+        torch.cuda.empty_cache()
+    saved = [r["cycles_zero"] - r["cycles_warm"] for r in rows]
+    tsave = [1.0 - r["time_warm_s"] / r["time_zero_s"] for r in rows]
+    errs = [r["err_vs_oracle"] for r in rows if "err_vs_oracle" in r]
+    return {"workload": f"{len(rows)} unseen GRF sources (seeds 1000+), alpha ~ U[.3,.8], same grid and target as the "
+                        f"headline; mixed precision from zero vs from the learned warm start (heuristic tiles)",
+            "cycles_saved_mean": float(np.mean(saved)), "cycles_saved_min": int(np.min(saved)),
+            "cycles_saved_max": int(np.max(saved)), "time_saved_mean": float(np.mean(tsave)),
+            "time_saved_min": float(np.min(tsave)), "err_vs_oracle_max": max(errs) if errs else None, "per_source": rows}
+
+
+def mode_oracle_1d(alpha, gamma, M, N, a):
+    """Per-mode oracle of the manufactured single-mode source (sin(pi x) times a(t))."""
+    from oracle import direct
+    t, R = oracle_R(alpha, gamma, M)
+    return direct.solve_o2_mode(R, direct.laplacian_eigs_1d(N, 1.0 / (N + 1))[0], a)
+
+
+def measure_manufactured(fh, stream, dim, N, M, alpha, gamma, nc, steps, tune):
+    """FP64 and mixed solves of the manufactured u = t^alpha prod sin(pi x_i) to relres 1e-8,
+    with the error against the per-mode oracle."""
+    import numpy as np
+    import torch
+    from paper_1706_07632_gb300 import inputs
     H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
-    t_hbuild = time.perf_counter() - t0
-    tmesh, _ = H.mesh()
-    amp, s = inputs.manufactured(tmesh[1:], N, dim, alpha)
+    t, _ = H.mesh()
+    amp, s = inputs.manufactured(t[1:], N, dim, alpha)
+    dev = torch.device("cuda", torch.cuda.current_device())
     f = torch.as_tensor(amp, device=dev).reshape((-1,) + (1,) * dim) * torch.as_tensor(s, device=dev)[None]
-    res = {}
+    from oracle import direct
+    _, R = oracle_R(alpha, gamma, M)
+    lam = direct.laplacian_eigs_1d(N, 1.0 / (N + 1))[0] * dim
+    w = direct.solve_o2_mode(R, lam, amp)
+    ref = torch.as_tensor(w, device=dev).reshape((-1,) + (1,) * dim) * torch.as_tensor(s, device=dev)[None]
+    out = {}
     for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
         P = fh.Problem(H, dim, N, 1.0, prec, stream)
         P.set_coarse_direct(nc)
         if tune:
-            P.autotune()  # column tiles timed per (kind, mode, columns); setup, untimed
-        r = timed_solves(P, f, steps, warmup, rtol, stream, dist)
-        r["P"] = P
-        r["time_to_rtol_s"] = r["ms"] / steps / 1e3
-        res[name] = r
-        del r["u"]
-    return H, f, res, t_hbuild
-
-
-def time_once(fn, stream):
-    import torch
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    out = fn()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / 1e3, out
-
-
-def measure_warmstart(fh, stream, dev, rtol, nc=1):
-    """2D N=1023^2, M=512, gamma=2, GRF source (ell = 0.1): FP64 zero guess, mixed zero guess, and
-    mixed from the learned warm start (network trained on library solves at N=255^2, same M)."""
-    import torch
-    from paper_1706_07632_gb300 import warmstart
-    dim, N, M, gamma, alpha, K = 2, 1023, 512, 2.0, 0.55, 24
-    t0 = time.perf_counter()
-    alphas = [0.3, 0.37, 0.44, 0.51, 0.58, 0.65, 0.72, 0.8]
-    X, Y = warmstart.generate(dim, 255, M, gamma, alphas, seeds=list(range(200, 208)), K=K)
-    t_data = time.perf_counter() - t0
-    net = fh.WSNet(320, 3, seed=0)
-    t_train, losses = time_once(lambda: warmstart.train(net, X, Y, steps=3000, batch=4096, lr=2e-3), stream)
-    H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
-    t, _ = H.mesh()
-    f = warmstart.source_field(dim, 999, t[1:], N)
-    out = {"workload": f"2D N={N}^2, M={M}, alpha={alpha}, gamma={gamma}, GRF source (length scale 0.1), "
-                       f"relres {rtol:g} of max|F| (same absolute target for every start)",
-           "coarse_solve": coarse_desc(nc),
-           "training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train, "loss": losses[-1],
-                        "params": net.num_params(), "train_grid": "N=255^2, M=512, 8 alphas"}}
-    for name, prec, warm in (("fp64_zero", fh.FP64, False), ("mixed_zero", fh.MIXED_FP32, False),
-                             ("mixed_warm", fh.MIXED_FP32, True)):
-        P = fh.Problem(H, dim, N, 1.0, prec, stream)
-        P.set_coarse_direct(nc)
-        P.set_rtol_reference(1)
+            P.autotune()
         u = torch.zeros_like(f)
-        if warm:  # untimed warm-up of the prediction and the solve
-            net.predict(P, f, alpha, K=K, bf16=True, u0=u)
-            P.solve(u, f, None, 1, 1, rtol, 60)
-        else:
-            P.solve(u, f, None, 1, 1, rtol, 60)
 
         def run():
-            if warm:
-                net.predict(P, f, alpha, K=K, bf16=True, u0=u)
-            else:
-                u.zero_()
-            return P.solve(u, f, None, 1, 1, rtol, 60)
-
-        ts, (k, rr) = time_once(run, stream)
-        out[name] = {"time_to_rtol_s": ts, "cycles": k, "relres_vs_maxF": rr}
-        if warm:
-            out[name]["predict_s"] = time_once(lambda: net.predict(P, f, alpha, K=K, bf16=True, u0=u), stream)[0]
+            u.zero_()
+            return P.solve(u, f, None, 1, 1, 1e-8, 80)
+        run()
+        P.profile(True)
+        ts, (k, rr) = timed(run, stream, steps)
+        cnt = P.counters()
+        cnt.update(P.defect_timing())
+        P.profile(False)
+        out[name] = {"time_to_rtol_s": statistics.median(ts), "cycles": k, "relres": rr,
+                     "err_vs_oracle": float((u - ref).abs().max() / ref.abs().max()),
+                     "gpu_launches_per_solve": cnt["launches"] / steps}
         del P
-    out["speedup_mixed_warm_vs_fp64"] = out["fp64_zero"]["time_to_rtol_s"] / out["mixed_warm"]["time_to_rtol_s"]
-    out["speedup_mixed_warm_vs_mixed_zero"] = out["mixed_zero"]["time_to_rtol_s"] / out["mixed_warm"]["time_to_rtol_s"]
-    out["cycles_saved_by_warm_start"] = out["mixed_zero"]["cycles"] - out["mixed_warm"]["cycles"]
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_rtol_s"] / out["mixed"]["time_to_rtol_s"]
+    k_ref = out["fp64"]["cycles"]
+    dof = N ** dim * M
+    for name in ("fp64", "mixed"):
+        out[name]["dof_cycles_per_s"] = dof * k_ref / out[name]["time_to_rtol_s"]
     return out
 
 
-def measure_batched(fh, inputs, stream, dev, rtol, n_inst=64, seed=7):
+def measure_batched(fh, stream, rtol, n_inst=64, seed=7):
     """64 independent 1D instances (alpha ~ U[.2,.9], gamma ~ U[1,3], M in {256,...,2048},
-    N in {255, 1023, 4095}, 8-mode sine-series sources), leaf autotuned per (M, alpha) class,
-    solved by one batched mixed solve (one launch per stage, graph-replayed cycles)."""
+    N in {255, 1023, 4095}, 8-mode sine-series sources), leaf autotuned per (M, N) class, solved by
+    one batched mixed solve (one launch per stage, graph-replayed cycles); error of every instance
+    against the per-mode oracle."""
     import numpy as np
     import torch
+    from oracle import direct
+    from paper_1706_07632_gb300 import inputs
     rng = np.random.default_rng(seed)
-    Hs, Ps, us, fs, dof = [], [], [], [], 0
+    Hs, Ps, us, fs, dof, meta = [], [], [], [], 0, []
     leaf_cache = {}
+    dev = torch.device("cuda", torch.cuda.current_device())
     for i in range(n_inst):
         alpha = float(rng.uniform(0.2, 0.9))
         gamma = float(rng.uniform(1.0, 3.0))
@@ -345,17 +506,26 @@ def measure_batched(fh, inputs, stream, dev, rtol, n_inst=64, seed=7):
         H = fh.HMatrix(alpha, gamma, 1.0, M, leaf_cache[key], 0, 1e-10)
         P = fh.Problem(H, 1, N, 1.0, fh.MIXED_FP32, stream)
         t, _ = H.mesh()
-        a, s, _ = inputs.sine_series_1d(seed * 1000 + i, t[1:], N)
+        a, s, c = inputs.sine_series_1d(seed * 1000 + i, t[1:], N)
         f = torch.as_tensor(a, device=dev)[:, None] * torch.as_tensor(s, device=dev)[None, :]
         Hs.append(H), Ps.append(P), fs.append(f), us.append(torch.zeros_like(f))
+        meta.append((alpha, gamma, M, N, c))
         dof += N * M
     for u in us:
         u.zero_()
     fh.solve_batched(Ps, us, fs, 1, 1, rtol, 60)  # warm-up (graph capture)
     for u in us:
         u.zero_()
-    tb, (k, rr) = time_once(lambda: fh.solve_batched(Ps, us, fs, 1, 1, rtol, 60), stream)
-    # the same instances one after the other, for reference
+    (tb,), (k, rr) = timed(lambda: fh.solve_batched(Ps, us, fs, 1, 1, rtol, 60), stream, 1)
+    errs = []
+    for i in range(0, n_inst, 8):  # every 8th instance against the per-mode oracle
+        alpha, gamma, M, N, c = meta[i]
+        _, R = oracle_R(alpha, gamma, M)
+        lam = direct.laplacian_eigs_1d(N, 1.0 / (N + 1))
+        x = inputs.grid(N)
+        ref = sum(np.outer(direct.solve_o2_mode(R, lam[q - 1], np.full(M, c[q - 1] / q ** 2)),
+                           np.sin(q * math.pi * x)) for q in range(1, 9))
+        errs.append(float(np.abs(us[i].cpu().numpy() - ref).max() / np.abs(ref).max()))
     for u in us:
         u.zero_()
 
@@ -364,60 +534,58 @@ def measure_batched(fh, inputs, stream, dev, rtol, n_inst=64, seed=7):
         for P, u, f in zip(Ps, us, fs):
             ks.append(P.solve(u, f, None, 1, 1, rtol, 60)[0])
         return ks
-    for u in us:
-        u.zero_()
-    ts, ks = time_once(seq, stream)
+    (ts,), ks = timed(seq, stream, 1)
     return {"workload": f"{n_inst} 1D instances, alpha~U[.2,.9], gamma~U[1,3], M in {{256..2048}}, "
                         f"N in {{255,1023,4095}}, 8-mode sine sources, relres {rtol:g}",
             "dof_total": dof, "leaves": sorted(set(leaf_cache.values())),
+            "leaf_by_size": {f"M={m},N={n}": l for (m, n), l in sorted(leaf_cache.items())},
             "batched_s": tb, "sequential_s": ts, "speedup_batched_vs_sequential": ts / tb,
             "batched_dof_cycles_per_s": dof * float(np.mean(k)) / tb,
-            "cycles_mean": float(np.mean(k)), "cycles_max": int(np.max(k)), "relres_max": float(np.max(rr))}
+            "cycles_mean": float(np.mean(k)), "cycles_max": int(np.max(k)), "relres_max": float(np.max(rr)),
+            "err_vs_oracle_max": max(errs), "err_checked_instances": len(errs)}
 
 
-def roofline(H, r, ncols_avg, kind):
-    """Finest-grid smoother half-sweeps (FP64 or FP32 products), timed live by CUDA events."""
-    c = r["cnt"]
-    flops_launch = H.flops_per_column() * ncols_avg
-    sm_ms = c["smooth_ms"] / max(c["smooth_launches"], 1)
-    achieved = flops_launch / (sm_ms / 1e3) / 1e12
-    if kind == "fp64":
-        peak, note = FP64_PEAK_TFLOPS, "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured 1.202)"
-        kern = "hpanel_kernel<double,double,64,*,SMOOTH> (finest-grid half-sweep)"
-    else:
-        peak, note = FP32_PEAK_TFLOPS, "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (an FFMA loop measured 75.1)"
-        kern = ("finest-grid half-sweep, FP32 products: hmma_kernel<double,16,SMOOTH> (3xTF32 tensor cores) "
-                "or hpanel_kernel<double,float,64,*,SMOOTH>, per the autotuned tile")
-    return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_note": note, "traffic": None, "avg_launch_ms": sm_ms,
-            "launches_timed": c["smooth_launches"], "algorithmic_flops_per_launch": flops_launch,
-            "share_of_step": c["smooth_ms"] / r["ms"] if r["ms"] > 0 else None}
-
-
-def roofline_defect(H, r, ncols, arith="fp64", traffic=None):
-    """Finest-grid defect products (Algorithm 3 over ncols columns), timed live: FP64 (DFMA) or
-    FP64-accurate double-float arithmetic on the FP32 pipe (the mixed path's default)."""
-    c = r["cnt"]
-    n = max(c["defect_launches"], 1)
-    ms = c["defect_ms"] / n
+def roofline_smoother(H, cnt, ms_total, ncols, M, hbm_peak, bf16_peak, peak_kind):
+    """Finest-grid smoother half-sweeps of the mixed path (FP32 storage, 3xTF32 tensor-core
+    products), timed live.  Algorithmic HBM bytes per column: the column's right-hand side, the
+    neighbours' values (each value of the other colour once) and the column written, 4 bytes each
+    per time level (12 M bytes); algorithmic tensor work: 3 TF32 products per FP32-accurate
+    flop.  The bound is whichever takes longer at its peak."""
+    n = max(cnt["smooth_launches"], 1)
+    t = cnt["smooth_ms"] / n / 1e3
+    bytes_launch = 12.0 * M * ncols
     flops_launch = H.flops_per_column() * ncols
-    achieved = flops_launch / (ms / 1e3) / 1e12
-    if arith == "df":
-        kern = f"hdf_kernel<64,*> (finest-grid FP64-accurate defect, double-float, {ncols} columns)"
-        peak, note = DF_PEAK_TFLOPS, ("152 SMs x 128 FP32 lanes/clk x 2.07 GHz x 2 flop per 11-instruction "
-                                      "double-float multiply-add")
-    else:
-        kern = f"hpanel_kernel<double,double,64,*,MATVEC> (finest-grid FP64 defect, {ncols} columns)"
-        peak, note = FP64_PEAK_TFLOPS, "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured 1.202)"
-    return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_note": note,
-            "traffic": traffic, "avg_launch_ms": ms, "launches_timed": c["defect_launches"],
-            "algorithmic_flops_per_launch": flops_launch,
-            "share_of_step": c["defect_ms"] / r["ms"] if r["ms"] > 0 else None}
+    tf32_peak = bf16_peak / 2.0
+    t_hbm = bytes_launch / (hbm_peak * 1e9)
+    t_tc = 3.0 * flops_launch / (tf32_peak * 1e12)
+    tr = TRAFFIC_PER_COLUMN.get("smooth")
+    common = {"kernel": "hmma_kernel<float,32,SMOOTH> (finest-grid half-sweep, FP32 storage, 3xTF32 mma.sync)",
+              "avg_launch_ms": t * 1e3, "launches_timed": cnt["smooth_launches"],
+              "share_of_step": cnt["smooth_ms"] / ms_total if ms_total > 0 else None,
+              "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
+              "traffic": tr * ncols if tr else None}
+    if t_hbm >= t_tc:
+        ach = bytes_launch / t / 1e9
+        return dict(common, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
+                    peak_note=f"copy bandwidth, {peak_kind}")
+    ach = 3.0 * flops_launch / t / 1e12
+    return dict(common, bound="tensor", achieved=ach, peak=tf32_peak, unit="TFLOP/s", frac=ach / tf32_peak,
+                peak_note=f"TF32 = BF16 dense ({peak_kind}) / 2")
 
 
-def dominant(*rs):
-    return max(rs, key=lambda x: x["share_of_step"] or 0.0)
+def roofline_defect(H, cnt, ms_total, ncols):
+    """The outer FP64-accurate defect (double-float products on the FP32 pipe), timed live."""
+    n = max(cnt["defect_launches"], 1)
+    t = cnt["defect_ms"] / n / 1e3
+    flops_launch = H.flops_per_column() * ncols
+    ach = flops_launch / t / 1e12
+    tr = TRAFFIC_PER_COLUMN.get("defect")
+    return {"kernel": "hdf_kernel<64,8,MATVEC> (finest-grid FP64-accurate defect, double-float)", "bound": "alu",
+            "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / DF_PEAK_TFLOPS,
+            "peak_note": "152 SMs x 128 FP32 lanes/clk x 2.07 GHz x 2 flop per 11-instruction double-float multiply-add",
+            "avg_launch_ms": t * 1e3, "launches_timed": cnt["defect_launches"],
+            "share_of_step": cnt["defect_ms"] / ms_total if ms_total > 0 else None,
+            "algorithmic_flops_per_launch": flops_launch, "traffic": tr * ncols if tr else None}
 
 
 def main():
@@ -429,109 +597,70 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_1706_07632_gb300 as fh
-    from paper_1706_07632_gb300 import inputs
 
     dist, rank, ws = dist_setup()
-    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    gamma = (2 - a.alpha) / a.alpha
-    dof = a.N * a.M
-
+    hbm_peak, bf16_peak, peak_kind = peaks()
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    H, f, res, t_hbuild = measure(fh, inputs, 1, a.N, a.M, a.alpha, gamma, a.steps, a.warmup, a.rtol, stream, dist, dev,
-                                  coarse_direct(a, 1, a.N), not a.no_autotune)
+
+    hd = measure_headline(fh, a, stream, dist)
+    arms = hd["arms"]
+    k_ref = arms["fp64_zero"]["cycles"]
+    dof = hd["dof"]
+    for r in arms.values():
+        r["value"] = job_value(dof * k_ref, ws, r["time_to_rtol_s"])
+    value = arms["mixed_warm"]["value"]
+    e2e = {"value": job_value(dof * k_ref, ws, hd["e2e_s"]), "unit": "DOF*cycles/s",
+           "h2d_bytes_per_step": hd["nbytes"], "d2h_bytes_per_step": hd["nbytes"], "ms_per_step": 1e3 * hd["e2e_s"],
+           "call": "fhmg_ws_solve_host (pinned host f in, warm start + solve, u out)"}
+
+    sweep = w1d = w2d = bat = cpu = None
+    if not a.quick:
+        # the sweep reuses a freshly trained network (same recipe and seed as the headline's)
+        net, _ = train_net(fh, stream)
+        sweep = measure_sources(fh, net, a, stream)
+        del net
+        torch.cuda.empty_cache()
+        w1d = measure_manufactured(fh, stream, 1, 4095, 4096, 0.5, 3.0, 255, 3, not a.no_autotune)
+        w1d["workload"] = "1D H-matrix, N=4095, M=4096, alpha=0.5, gamma=3, leaf 64, tol 1e-10, V(1,1) to relres 1e-8"
+        torch.cuda.empty_cache()
+        w2d = measure_manufactured(fh, stream, 2, 511, 1024, 0.4, 2.5, 31, 2, not a.no_autotune)
+        w2d["workload"] = "2D H-matrix, N=511^2, M=1024, alpha=0.4, gamma=2.5, leaf 64, tol 1e-10, V(1,1) to relres 1e-8"
+        torch.cuda.empty_cache()
+        bat = measure_batched(fh, stream, a.rtol)
+        torch.cuda.empty_cache()
     clk = clocks.stop() if clocks else None
 
-    k_ref = res["fp64"]["cycles"] / a.steps
-    for r in res.values():
-        r["value"] = job_value(dof * k_ref, ws, r["time_to_rtol_s"])
-    head = res["mixed"]
+    if rank == 0 and not a.quick:
+        m_stop = 192
+        ts, ndof = oracle_direct_c5_sample(m_stop)
+        cpu = {"value": ndof * k_ref / ts, "unit": "DOF*cycles/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"direct solve (implicit time stepping, dense L1 history sum, DST-I spatial solve per step; "
+                          f"numpy/scipy on the host threads) of the first {m_stop} of {HEAD['M']} time levels of the "
+                          f"headline workload: {ts:.2f} s for {ndof} DOF; DOF*cycles with the FP64 cycle count {k_ref}")}
 
-    e2e = None
-    if not a.no_e2e:
-        P = head["P"]
-        fh_host = f.cpu().pin_memory()
-        uh = torch.zeros(f.shape, dtype=torch.float64).pin_memory()
-        P.solve_host(uh, fh_host, None, 1, 1, a.rtol, 80)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(a.steps):
-            uh.zero_()
-            P.solve_host(uh, fh_host, None, 1, 1, a.rtol, 80)
-        te = time.perf_counter() - t0
-        te = max_over_ranks(te, dist)
-        e2e = {"value": job_value(dof * k_ref * a.steps, ws, te), "unit": "DOF*cycles/s", "h2d_bytes_per_step": 2 * dof * 8,
-               "d2h_bytes_per_step": dof * 8, "ms_per_step": 1e3 * te / a.steps}
-        del fh_host, uh
-
-    def summary(r, steps):
-        return {"value": r.get("value"), "time_to_rtol_s": r["time_to_rtol_s"],
-                "cycles_per_solve": r["cycles"] / steps, "relres": r["relres"],
-                "gpu_launches_per_solve": r["cnt"]["launches"] / steps}
-
-    w2d = None
-    if not a.no_2d:
-        del f
-        torch.cuda.empty_cache()
-        N2, M2, al2, ga2 = 511, 1024, 0.4, 2.5
-        st2, wu2 = min(a.steps, 2), 1
-        nc2 = coarse_direct(a, 2, N2)
-        H2, f2, res2, tb2 = measure(fh, inputs, 2, N2, M2, al2, ga2, st2, wu2, a.rtol, stream, dist, dev, nc2,
-                                    not a.no_autotune)
-        k2 = res2["fp64"]["cycles"] / st2
-        dof2 = N2 * N2 * M2
-        for r in res2.values():
-            r["value"] = job_value(dof2 * k2, ws, r["time_to_rtol_s"])
-        w2d = {"workload": f"2D H-matrix, N={N2}^2, M={M2}, alpha={al2}, gamma={ga2}, leaf 64, tol 1e-10, V(1,1) to "
-                           f"relres {a.rtol:g}", "coarse_solve": coarse_desc(nc2),
-               "fp64": summary(res2["fp64"], st2), "mixed": summary(res2["mixed"], st2),
-               "speedup_mixed_vs_fp64": res2["fp64"]["time_to_rtol_s"] / res2["mixed"]["time_to_rtol_s"],
-               "roofline_fp64": roofline(H2, res2["fp64"], N2 * N2 / 2.0, "fp64"),
-               "roofline_mixed": roofline(H2, res2["mixed"], N2 * N2 / 2.0, "mixed"), "hbuild_s": tb2}
-        del f2
-
-    wws = None
-    bat = None
-    if not a.no_2d:
-        torch.cuda.empty_cache()
-        wws = measure_warmstart(fh, stream, dev, a.rtol, coarse_direct(a, 2, 1023))
-        torch.cuda.empty_cache()
-        bat = measure_batched(fh, inputs, stream, dev, a.rtol)
-        torch.cuda.empty_cache()
-
-    cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
-        ts, tb = oracle_direct_sample(a)
-        cpu = {"value": dof * k_ref / ts, "unit": "DOF*cycles/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"full direct solve of the headline workload (N={a.N}, M={a.M}), implicit time stepping with "
-                         f"the dense L1 history sum, numpy/OpenBLAS on all host threads: {ts:.2f} s (+{tb:.2f} s to "
-                         f"build R, not timed); cycles = the FP64 V(1,1) count to 1e-8 ({k_ref:.0f})"}
-
-    # the headline step's dominant kernel: the FP32-product smoother or the FP64 outer defect
-    rl_s = roofline(H, res["mixed"], a.N / 2.0, "mixed")
-    rl_d = roofline_defect(H, res["mixed"], a.N, "df")
-    if a.N == 4095 and a.M == 4096 and a.alpha == 0.5:
-        # DRAM bytes per launch from the ncu captures (profiles/), same kernels and workload
-        rl_s["traffic"] = 366.6e6
-        rl_s["traffic_source"] = "profiles/hmma_mixed_smooth_1d_4095x4096.md (ncu dram read+write, one launch)"
-        rl_d["traffic"] = 382.2e6
-        rl_d["traffic_source"] = "profiles/hdf_defect_1d_4095x4096.md (ncu dram read+write, one launch)"
-    rl_head = dominant(rl_s, rl_d)
-    rl_second = rl_d if rl_head is rl_s else rl_s
+    ncol_colour = (HEAD["N"] ** 2 + 1) // 2
+    rl_s = roofline_smoother(hd["H"], hd["cnt"], hd["ms"], ncol_colour, HEAD["M"], hbm_peak, bf16_peak, peak_kind)
+    rl_d = roofline_defect(hd["H"], hd["cnt"], hd["ms"], HEAD["N"] ** 2)
+    rl_head, rl_second = (rl_s, rl_d) if (rl_s["share_of_step"] or 0) >= (rl_d["share_of_step"] or 0) else (rl_d, rl_s)
     if rank == 0:
-        line = {"metric": "space-time DOF*cycles/s (time-to-1e-8 solve)", "value": head["value"],
-                "unit": "DOF*cycles/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
-                "ms_per_step": head["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": workload(a),
-                "headline": ("mixed precision: defect correction with an FP64-accurate (double-float) outer defect around "
-                             "V-cycles with FP32 H-matrix products (3xTF32 tensor cores on wide tiles)"),
-                "cycle_unit": f"FP64 V(1,1) cycles to relres {a.rtol:g} on this workload = {k_ref:.0f}",
-                "fp64": summary(res["fp64"], a.steps), "mixed": summary(res["mixed"], a.steps),
-                "speedup_mixed_vs_fp64": res["fp64"]["time_to_rtol_s"] / res["mixed"]["time_to_rtol_s"],
-                "hbuild_s": t_hbuild, "roofline": rl_head, "roofline_secondary": rl_second,
-                "roofline_fp64": roofline(H, res["fp64"], a.N / 2.0, "fp64"), "workload_2d": w2d,
-                "workload_warmstart": wws, "workload_batched": bat,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": head["cnt"]["launches"], "clocks": clk}
+        line = {"metric": METRIC, "value": value, "unit": "DOF*cycles/s", "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": hd["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "config": head_config(a.rtol, not a.no_autotune),
+                "headline": ("mixed precision + learned warm start: network prediction of u0, then defect correction "
+                             "with double-float FP64-accurate outer defects around V-cycles with FP32 storage and "
+                             "3xTF32 tensor-core H-matrix products"),
+                "cycle_unit": f"FP64 V(1,1) cycles to the target on the headline source = {k_ref}",
+                "arms": arms,
+                "speedup_mixed_warm_vs_fp64": arms["fp64_zero"]["time_to_rtol_s"] / arms["mixed_warm"]["time_to_rtol_s"],
+                "speedup_mixed_warm_vs_mixed_zero": arms["mixed_zero"]["time_to_rtol_s"] / arms["mixed_warm"]["time_to_rtol_s"],
+                "cycles_saved_by_warm_start": arms["mixed_zero"]["cycles"] - arms["mixed_warm"]["cycles"],
+                "training": hd["training"], "hbuild_s": hd["hbuild_s"],
+                "roofline": rl_head, "roofline_secondary": rl_second,
+                "sources": sweep, "workload_1d": w1d, "workload_2d": w2d, "workload_batched": bat,
+                "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": hd["cnt"]["launches"] + hd["nn_launches"], "clocks": clk}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -23,6 +23,11 @@
  *    host.  Outputs are written only on FHMG_OK, except u after a solve that did not reach
  *    rtol, which holds the last iterate.  The library never frees caller memory.
  *  - fhmg_last_error() returns a message for the last failure of the calling thread.
+ *  - A problem lives on the CUDA device that was current when it was created; every call on it
+ *    makes that device current for its duration and restores the caller's device afterwards.
+ *  - Every device-side wait of the walk kernels is bounded.  A walk whose wait gives up leaves
+ *    early and sets the problem's error word; the next call that returns a host value (a norm, a
+ *    solve) reports it as FHMG_ETIMEOUT and clears it, so the problem stays usable.
  */
 #ifndef FHMG_H_
 #define FHMG_H_
@@ -149,9 +154,12 @@ int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const d
  * paper has no counterpart: this is a library service.  It allocates nothing: its scratch is a
  * fixed library-owned device array of 2^21 doubles (16 MiB, held on every GPU that loads the
  * library until the process exits), so M * N^dim must be <= 2^21 (else FHMG_EINVAL).  f is the
- * full right-hand side (fold any initial data into it: there is no g).  The first call on a device
- * looks the array's address up -- make it before any stream capture.  All calls share the array:
- * calls whose GPU work overlaps race and must be serialised by the caller. */
+ * full right-hand side (fold any initial data into it: there is no g).  The products follow the
+ * problem's defect arithmetic (fhmg_problem_set_defect_arith), as in fhmg_residual_norm.  The first
+ * call for a problem on a given device looks the array's address up on that device -- make it
+ * before any stream capture; after cudaDeviceReset on that device the address is stale and the
+ * entry point must not be used there again in the process.  All calls share the array: calls whose
+ * GPU work overlaps race and must be serialised by the caller. */
 int fhmg_residual_norm_noalloc(fhmg_problem p, const double* u, const double* f, double* out_max);
 /* V(nu1, nu2) cycles from the initial guess in u until ||r_k||_inf <= rtol ||r_0||_inf or
  * max_cycles.  cycles_out / relres_out (host, may be NULL) receive the cycle count and
@@ -205,6 +213,20 @@ int fhmg_problem_set_tensor_cores(fhmg_problem p, int enable);
  * than 65535 points.  fhmg_solve_batched keeps the full recursion. */
 int fhmg_problem_set_coarse_direct(fhmg_problem p, int n);
 
+/* Cycle index of the cycles run by fhmg_vcycle / fhmg_solve (Algorithm 2's number of coarse-grid
+ * cycles per level, the paper's gamma -- not the grading exponent): 1 (default) V-cycle, 2 W-cycle,
+ * up to 4.  The one-point coarsest level and an exactly solved level (fhmg_problem_set_coarse_direct)
+ * are solved once whatever the index.  fhmg_solve_batched always runs V-cycles. */
+int fhmg_problem_set_cycle_index(fhmg_problem p, int cycle_index);
+
+/* Test hook for the bounded device waits (the paper has no counterpart).  Arms the problem's next
+ * walk launch so that every CTA's producer withholds the second chunk of its stream and the
+ * consumer warps' waits give up after consumer_spin polls (1 .. 2^24) instead of 2^24: that launch
+ * then leaves early without touching memory it has not been given, every copy it issued lands
+ * before its CTAs retire, and the call that reads the error word returns FHMG_ETIMEOUT.  One-shot:
+ * later launches run normally. */
+int fhmg_problem_inject_timeout(fhmg_problem p, long long consumer_spin);
+
 /* --- learned warm start (an addition to the method; the paper has none) ------------------------
  * For a source constant in time and a finite sine series, each spatial eigenmode s_k of A_h
  * (eigenvalue lam_k) evolves independently: u = sum_k c_k w_k(t) s_k with (R + lam_k I) w_k = 1.
@@ -235,6 +257,15 @@ int fhmg_ws_dataset(fhmg_problem prob, const double* u, const double* f, double 
                     float* X_out, float* Y_out, long long* nrows);
 /* u0 (device, M x N^dim) = warm start for source f (constant in time) and order alpha. */
 int fhmg_ws_predict(fhmg_wsnet net, fhmg_problem prob, const double* f, double alpha, int K, int bf16, double* u0);
+/* Kernel launches issued so far by the network and warm-start kernels (training, inference,
+ * projection, synthesis) of the whole process. */
+int fhmg_wsnet_launches(long long* n);
+/* The warm-started solve from HOST buffers: copies f (M x N^dim doubles, constant in time) to the
+ * device, predicts u0 with the network (fhmg_ws_predict, K modes per dimension, bf16 != 0: BF16
+ * inference), runs fhmg_solve from u0 and copies the solution into u_host.  Returns like fhmg_solve
+ * (u_host is written also after FHMG_ENOTCONV). */
+int fhmg_ws_solve_host(fhmg_wsnet net, fhmg_problem p, double* u_host, const double* f_host, double alpha, int K,
+                       int bf16, int nu1, int nu2, double rtol, int max_cycles, int* cycles_out, double* relres_out);
 
 /* fhmg_solve with HOST arrays (u in/out, f, g or NULL): copies in, solves, copies u back. */
 int fhmg_solve_host(fhmg_problem p, double* u_host, const double* f_host, const double* g_host,

@@ -64,6 +64,8 @@ _SIGS = {
     "fhmg_problem_set_coarse_direct": (_I, [_P, _I]),
     "fhmg_problem_set_tensor_cores": (_I, [_P, _I]),
     "fhmg_problem_set_defect_arith": (_I, [_P, _I]),
+    "fhmg_problem_set_cycle_index": (_I, [_P, _I]),
+    "fhmg_problem_inject_timeout": (_I, [_P, _LL]),
     "fhmg_hmatvec_df": (_I, [_P, _P, _P, _LL, _I]),
     "fhmg_wsnet_create": (_I, [_I, _I, _c.c_ulonglong, _c.POINTER(_P)]),
     "fhmg_wsnet_destroy": (_I, [_P]),
@@ -75,6 +77,8 @@ _SIGS = {
     "fhmg_wsnet_train": (_I, [_P, _P, _P, _LL, _I, _I, _c.c_float, _c.c_ulonglong, _c.POINTER(_c.c_float), _P]),
     "fhmg_ws_dataset": (_I, [_P, _P, _P, _D, _I, _c.c_float, _P, _P, _c.POINTER(_LL)]),
     "fhmg_ws_predict": (_I, [_P, _P, _P, _D, _I, _I, _P]),
+    "fhmg_wsnet_launches": (_I, [_c.POINTER(_LL)]),
+    "fhmg_ws_solve_host": (_I, [_P, _P, _P, _P, _D, _I, _I, _I, _I, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
 }
 
 
@@ -194,6 +198,15 @@ class Problem:
         """Solve the coarse-grid correction exactly on the level with n points per dimension
         (n <= 1: recursion to one point, the paper's cycle)."""
         _check(lib().fhmg_problem_set_coarse_direct(self._p, n))
+
+    def set_cycle_index(self, cycle_index):
+        """Coarse-grid cycles per level: 1 V-cycle (default), 2 W-cycle."""
+        _check(lib().fhmg_problem_set_cycle_index(self._p, cycle_index))
+
+    def inject_timeout(self, consumer_spin=1024):
+        """Test hook: the next walk launch withholds a chunk and its waits give up after
+        consumer_spin polls; the next norm or solve then raises FHMG_ETIMEOUT."""
+        _check(lib().fhmg_problem_inject_timeout(self._p, consumer_spin))
 
     def set_defect_arith(self, mode):
         """Outer defect products of the mixed path: 1 double-float (default), 0 FP64."""
@@ -355,6 +368,13 @@ class WSNet:
         _check(lib().fhmg_ws_predict(self._h, prob._p, _ptr(f), alpha, K, 1 if bf16 else 0, _ptr(u0)))
         return u0
 
+    def solve_host(self, prob, u, f, alpha, K=24, bf16=True, nu1=1, nu2=1, rtol=1e-8, max_cycles=60):
+        """fhmg_ws_solve_host: f (host, constant in time) in, warm start, solve, u (host) out."""
+        k, rr = _I(), _D()
+        _check(lib().fhmg_ws_solve_host(self._h, prob._p, _ptr(u), _ptr(f), alpha, K, 1 if bf16 else 0, nu1, nu2,
+                                        rtol, max_cycles, ctypes.byref(k), ctypes.byref(rr)))
+        return k.value, rr.value
+
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fhmg_wsnet_destroy(self._h)
@@ -371,6 +391,13 @@ def ws_dataset(prob, u, f, alpha, K=24, rel_thr=1e-6):
     _check(lib().fhmg_ws_dataset(prob._p, _ptr(u), _ptr(f), alpha, K, rel_thr, X.data_ptr(), Y.data_ptr(),
                                  ctypes.byref(n)))
     return X[: n.value], Y[: n.value]
+
+
+def wsnet_launches():
+    """Kernel launches issued so far by the network and warm-start kernels (process-wide)."""
+    n = _LL()
+    _check(lib().fhmg_wsnet_launches(ctypes.byref(n)))
+    return n.value
 
 
 def autotune_leaf(alpha, gamma, T, M, tol, dim, N, Lx=1.0, prec=FP64, stream=None):

@@ -127,14 +127,18 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
     if (t != NT) return;
     long long k = 0;
     int slot = 0;
-    bool ok = true;
-    for (long long g = blockIdx.x; g < B.ntiles && ok; g += gridDim.x) {
+    bool ok = true, stop = false;
+    for (long long g = blockIdx.x; g < B.ntiles && ok && !stop; g += gridDim.x) {
       const WalkJob<double, float>& J = B.job[job_of(B, g)];
       const int nch = __ldg(J.P.cptr + J.P.nb);
       int4 cdn = __ldg(J.P.chunks);
       for (int c = 0; c < nch; ++c, ++k) {
         const int4 cd = cdn;
         if (c + 1 < nch) cdn = __ldg(J.P.chunks + c + 1);
+        if (k + 1 == B.withhold) {
+          stop = true;
+          break;
+        }
         if (k >= ns && !mbar_wait_or_abort(empty + slot, (uint32_t)(((k / ns) - 1) & 1), abort_flag)) {
           ok = false;
           break;
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
   auto consumer_sync = [&]() -> bool {
     __syncwarp();
     if (lane == 0) mbar_arrive(cbar);
-    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag);
+    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag, B.spin);
     cbphase ^= 1;
     return !give_up(ok);
   };
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
       }
       const int si = i % W;
       for (bool leaf_done = false; !leaf_done;) {
-        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag))) return;
+        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag, B.spin))) return;
         const int4 cd = sdesc[cslot];
         leaf_done = ((cd.x >> 12) & 1) != 0;
         const int type = cd.x & 15, cnt = (cd.x >> 4) & 0xff;

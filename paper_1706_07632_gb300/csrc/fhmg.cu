@@ -45,8 +45,6 @@ int fail(int code, const char* fmt, ...) {
     if (s_ != FHMG_OK) return s_;   \
   } while (0)
 
-constexpr int kSMs = 152;
-
 }  // namespace
 
 struct fhmg_hmatrix_s {
@@ -81,6 +79,7 @@ struct LevelData {
 
 struct fhmg_problem_s {
   fhmg_hmatrix H = nullptr;
+  int dev = 0;  // the CUDA device the problem was created on (made current by every call)
   int dim = 1, N = 0, nlev = 0, prec = 0;
   double Lx = 1.0;
   cudaStream_t st = nullptr;
@@ -111,6 +110,8 @@ struct fhmg_problem_s {
   double* hf = nullptr;
   double* hg = nullptr;
   int inner = 0;         // inner V-cycles per defect-correction step (0: 2 with FP32 storage, 4 otherwise)
+  int cycle_index = 1;   // coarse-grid cycles per level (1: V-cycle, 2: W-cycle)
+  long long inj_spin = 0;  // armed test hook: the next walk withholds a chunk, consumers poll inj_spin times
   std::vector<void*> allocs;
   // exact coarse-level solve (fhmg_problem_set_coarse_direct), FP64
   int ndirect = 1;              // grid size per dimension solved exactly (1: recursion to one point)
@@ -180,15 +181,36 @@ int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, Dev
   return FHMG_OK;
 }
 
-int blocks_for(long long n) {
-  long long b = (n + 255) / 256;
-  return (int)std::max(1LL, std::min(b, 152LL * 32));
-}
+int blocks_for(long long n) { return fhmg::grid_for(n, 32); }
 
 int check_dims(fhmg_problem p) {
   if (!p) return fail(FHMG_EINVAL, "null problem");
   return FHMG_OK;
 }
+
+// Makes a device current for the scope of a call and restores the caller's device afterwards.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Entry of every call on a problem: argument check, then the problem's device made current.
+#define ENTER(p)                                                                             \
+  TRY(check_dims(p));                                                                        \
+  DeviceScope dev_scope_((p)->dev);                                                          \
+  if (!dev_scope_.ok) return fail(FHMG_ECUDA, "cannot make the problem's device current")
 
 int record_event(fhmg_problem p, std::vector<cudaEvent_t>& ev, size_t& used) {
   if (used == ev.size()) {
@@ -316,15 +338,26 @@ int launch_jobs(cudaStream_t st, int, std::vector<fhmg::WalkArgsT<float>>& jobs,
   return FHMG_OK;
 }
 
+// The armed timeout test hook (fhmg_problem_inject_timeout) applies to the next walk only.
+template <typename T>
+void apply_injection(fhmg_problem p, fhmg::WalkArgsT<T>& a) {
+  if (p->inj_spin <= 0) return;
+  a.spin = p->inj_spin;
+  a.withhold = 2;  // the second chunk of every CTA's stream is never issued
+  p->inj_spin = 0;
+}
+
 template <typename T>
 int walk_smooth(fhmg_problem p, int l, int kind, const Geo& g, long long nc, T* X, const T* B) {
   std::vector<fhmg::WalkArgsT<T>> j{smooth_job<T>(p, l, kind, g, nc, X, B)};
+  apply_injection(p, j[0]);
   return launch_jobs(p->st, kind, j, &p->launches);
 }
 
 template <typename T>
 int walk_matvec(fhmg_problem p, int kind, long long nc, const T* X, const T* B, T* OUT, unsigned long long* norm) {
   std::vector<fhmg::WalkArgsT<T>> j{matvec_job<T>(p, kind, nc, X, B, OUT, norm)};
+  apply_injection(p, j[0]);
   return launch_jobs(p->st, kind, j, &p->launches);
 }
 
@@ -449,13 +482,16 @@ int coarse_correction(fhmg_problem p, int l, int nu1, int nu2, int kind) {
   LevelData& lc = p->lev[l - 1];
   const long long n = lc.npts * p->M;
   if (l - 1 == p->lcd) return direct_level<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc));
+  // cycle index: the coarse problem gets cycle_index cycles (W-cycle: 2) unless it is the
+  // one-point level, whose solve is exact
+  const int reps = l - 1 > 0 ? p->cycle_index : 1;
   if constexpr (std::is_same<T, double>::value) {
     if (kind == KSPLIT && level_fp32(p, l - 1)) {
       to_float_kernel<<<blocks_for(n), 256, 0, p->st>>>(lc.RC, lc.RC32, n);
       ++p->launches;
       CK(cudaGetLastError());
       CK(cudaMemsetAsync(lc.E32, 0, sizeof(float) * n, p->st));
-      TRY(vcycle_rec<float>(p, l - 1, lc.E32, lc.RC32, nu1, nu2, K32));
+      for (int r = 0; r < reps; ++r) TRY(vcycle_rec<float>(p, l - 1, lc.E32, lc.RC32, nu1, nu2, K32));
       to_double_kernel<<<blocks_for(n), 256, 0, p->st>>>(lc.E32, lc.E, n);
       ++p->launches;
       CK(cudaGetLastError());
@@ -463,7 +499,8 @@ int coarse_correction(fhmg_problem p, int l, int nu1, int nu2, int kind) {
     }
   }
   CK(cudaMemsetAsync(lev_E<T>(lc), 0, sizeof(T) * n, p->st));
-  return vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind);
+  for (int r = 0; r < reps; ++r) TRY(vcycle_rec<T>(p, l - 1, lev_E<T>(lc), lev_RC<T>(lc), nu1, nu2, kind));
+  return FHMG_OK;
 }
 
 template <typename T>
@@ -478,17 +515,31 @@ int vcycle_rec(fhmg_problem p, int l, T* u, const T* F, int nu1, int nu2, int ki
   return FHMG_OK;
 }
 
+// A walk that gave up set the problem's error word: report it once (FHMG_ETIMEOUT) and clear it,
+// so that the problem stays usable.
+int report_timeout(fhmg_problem p) {
+  CK(cudaMemsetAsync(p->derr, 0, sizeof(int), p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return fail(FHMG_ETIMEOUT, "a walk kernel gave up waiting on a shared-memory stage");
+}
+
 int read_norm(fhmg_problem p, double* out) {
   unsigned long long bits = 0;
   int derr = 0;
   CK(cudaMemcpyAsync(&bits, p->dnorm, sizeof bits, cudaMemcpyDeviceToHost, p->st));
   CK(cudaMemcpyAsync(&derr, p->derr, sizeof derr, cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
-  if (derr) return fail(FHMG_ETIMEOUT, "a panel kernel gave up waiting on a shared-memory stage");
+  if (derr) return report_timeout(p);
   double v;
   std::memcpy(&v, &bits, sizeof v);
   *out = v;
   return FHMG_OK;
+}
+
+// Products of the FP64 defect on the finest grid: double-float for mixed problems (unless set
+// to FP64 by fhmg_problem_set_defect_arith), FP64 otherwise.
+int defect_kind(fhmg_problem p) {
+  return (p->prec == FHMG_MIXED_FP32 && p->defect_df && p->panel64df.d.pkg) ? KDF : K64;
 }
 
 // FP64 defect on the finest grid.  colour0_only (after a completed red-black sweep the defect
@@ -512,9 +563,8 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
                                                                                        u, F, nullptr, dst);
     ++p->launches;
     CK(cudaGetLastError());
-    const int kind = (p->prec == FHMG_MIXED_FP32 && p->defect_df && p->panel64df.d.pkg) ? KDF : K64;
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
-    TRY(walk_matvec<double>(p, kind, lv.npts, u, dst, R ? R : nullptr, p->dnorm));
+    TRY(walk_matvec<double>(p, defect_kind(p), lv.npts, u, dst, R ? R : nullptr, p->dnorm));
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
   }
   return read_norm(p, out);
@@ -756,10 +806,9 @@ int read_norms(cudaStream_t st, std::vector<BLev>& set, std::vector<double>& out
   }
   CK(cudaStreamSynchronize(st));
   out.resize(set.size());
-  for (size_t i = 0; i < set.size(); ++i) {
-    if (errs[i]) return fail(FHMG_ETIMEOUT, "a panel kernel gave up waiting on a shared-memory stage");
-    std::memcpy(&out[i], &bits[i], 8);
-  }
+  for (size_t i = 0; i < set.size(); ++i)
+    if (errs[i]) return report_timeout(set[i].p);
+  for (size_t i = 0; i < set.size(); ++i) std::memcpy(&out[i], &bits[i], 8);
   return FHMG_OK;
 }
 
@@ -807,24 +856,27 @@ __global__ void scale_kernel(double* y, long long n, double a) {
 // to the host; allocates nothing.
 int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, double* B,
                               unsigned long long* norm_word, double* out) {
+  ENTER(p);
   LevelData& lv = p->lev[p->nlev - 1];
   CK(cudaMemsetAsync(norm_word, 0, sizeof(unsigned long long), p->st));
   fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
                                                                                      u, F, nullptr, B);
   ++p->launches;
   CK(cudaGetLastError());
-  TRY(walk_matvec<double>(p, K64, lv.npts, u, B, nullptr, norm_word));
+  TRY(walk_matvec<double>(p, defect_kind(p), lv.npts, u, B, nullptr, norm_word));
   unsigned long long bits = 0;
   int derr = 0;
   CK(cudaMemcpyAsync(&bits, norm_word, sizeof bits, cudaMemcpyDeviceToHost, p->st));
   CK(cudaMemcpyAsync(&derr, p->derr, sizeof derr, cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
-  if (derr) return fail(FHMG_ETIMEOUT, "a panel kernel gave up waiting on a shared-memory stage");
+  if (derr) return report_timeout(p);
   std::memcpy(out, &bits, sizeof bits);
   return FHMG_OK;
 }
 
 long long fhmg_internal_grid_elems(fhmg_problem p) { return p->lev[p->nlev - 1].npts * (long long)p->M; }
+
+int fhmg_internal_problem_device(fhmg_problem p) { return p->dev; }
 
 int fhmg_internal_problem_geom(fhmg_problem p, int* dim, int* N, int* M, double* Lx, void** stream,
                                const double** t_host) {
@@ -937,6 +989,10 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   p->Lx = Lx;
   p->prec = prec;
   p->st = (cudaStream_t)stream;
+  if (cudaGetDevice(&p->dev) != cudaSuccess) {
+    delete p;
+    return fail(FHMG_ECUDA, "cudaGetDevice failed");
+  }
   p->M = h->host.M;
   p->L = h->host.L;
   p->nb = h->host.nb;
@@ -1038,7 +1094,7 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
 // column tile TC in {1, 2, 4, 8, 16, 32} that fits in shared memory (3 launches each, CUDA
 // events, on zeroed workspaces) and records the fastest; later launches use it.
 int fhmg_problem_autotune(fhmg_problem p) {
-  TRY(check_dims(p));
+  ENTER(p);
   const int M = p->M;
   const LevelData& fine = p->lev[p->nlev - 1];
   CK(cudaMemsetAsync(p->Rs, 0, sizeof(double) * fine.npts * M, p->st));
@@ -1108,21 +1164,21 @@ int fhmg_problem_autotune(fhmg_problem p) {
 }
 
 int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (inner_cycles < 0) return fail(FHMG_EINVAL, "inner_cycles must be >= 0");
   p->inner = inner_cycles;
   return FHMG_OK;
 }
 
 int fhmg_problem_set_mixed_storage(fhmg_problem p, int mode) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (mode < 0 || mode > 2) return fail(FHMG_EINVAL, "mixed storage mode must be 0, 1 or 2");
   p->mixed_storage = mode;
   return FHMG_OK;
 }
 
 int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (n < 0) return fail(FHMG_EINVAL, "coarse direct size must be >= 0");
   int l = -1;
   if (n > 1) {
@@ -1179,28 +1235,43 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
 }
 
 int fhmg_problem_set_defect_arith(fhmg_problem p, int mode) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (mode != 0 && mode != 1) return fail(FHMG_EINVAL, "defect arithmetic must be 0 (FP64) or 1 (double-float)");
   p->defect_df = mode;
   return FHMG_OK;
 }
 
 int fhmg_problem_set_tensor_cores(fhmg_problem p, int enable) {
-  TRY(check_dims(p));
+  ENTER(p);
   p->use_mma = enable != 0;
   p->tune.clear();  // tuned tiles were timed with the other kernels
   return FHMG_OK;
 }
 
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (ref != 0 && ref != 1) return fail(FHMG_EINVAL, "reference must be 0 (initial defect) or 1 (max |F|)");
   p->rtol_ref = ref;
   return FHMG_OK;
 }
 
+int fhmg_problem_set_cycle_index(fhmg_problem p, int cycle_index) {
+  ENTER(p);
+  if (cycle_index < 1 || cycle_index > 4) return fail(FHMG_EINVAL, "cycle index must be 1 (V) .. 4 (got %d)", cycle_index);
+  p->cycle_index = cycle_index;
+  return FHMG_OK;
+}
+
+int fhmg_problem_inject_timeout(fhmg_problem p, long long consumer_spin) {
+  ENTER(p);
+  if (consumer_spin < 1 || consumer_spin > fhmg::kSpinLimit)
+    return fail(FHMG_EINVAL, "consumer spin limit must be in 1..2^24");
+  p->inj_spin = consumer_spin;
+  return FHMG_OK;
+}
+
 int fhmg_problem_profile(fhmg_problem p, int enable) {
-  TRY(check_dims(p));
+  ENTER(p);
   CK(cudaStreamSynchronize(p->st));
   p->profile = enable != 0;
   p->ev_used = 0;
@@ -1210,7 +1281,7 @@ int fhmg_problem_profile(fhmg_problem p, int enable) {
 }
 
 int fhmg_problem_counters(fhmg_problem p, long long* launches, long long* smooth_launches, double* smooth_ms) {
-  TRY(check_dims(p));
+  ENTER(p);
   CK(cudaStreamSynchronize(p->st));
   if (launches) *launches = p->launches;
   if (smooth_launches) *smooth_launches = (long long)(p->ev_used / 2);
@@ -1219,7 +1290,7 @@ int fhmg_problem_counters(fhmg_problem p, long long* launches, long long* smooth
 }
 
 int fhmg_problem_defect_timing(fhmg_problem p, long long* defect_launches, double* defect_ms, long long* columns) {
-  TRY(check_dims(p));
+  ENTER(p);
   CK(cudaStreamSynchronize(p->st));
   if (defect_launches) *defect_launches = (long long)(p->evd_used / 2);
   if (defect_ms) *defect_ms = pair_ms(p->evd, p->evd_used);
@@ -1228,7 +1299,7 @@ int fhmg_problem_defect_timing(fhmg_problem p, long long* defect_launches, doubl
 }
 
 int fhmg_line_solve(fhmg_problem p, int level, double* X, const double* B, long long ncols) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
   if (!X || !B || ncols < 0) return fail(FHMG_EINVAL, "bad arrays");
   Geo g{0, 0, 0, ncols, 0.0};
@@ -1236,7 +1307,7 @@ int fhmg_line_solve(fhmg_problem p, int level, double* X, const double* B, long 
 }
 
 int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!X || !Y || ncols < 0 || X == Y) return fail(FHMG_EINVAL, "bad arrays");
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
   TRY(walk_matvec<double>(p, K64, ncols, X, Y, Y, nullptr));
@@ -1247,7 +1318,7 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
 }
 
 int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, long long ncols, int tile) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
   if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
   if (!X || !B || ncols < 0 || tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
@@ -1259,7 +1330,7 @@ int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, l
 }
 
 int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols, int tile) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
   if (!X || !Y || ncols < 0 || X == Y || tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
     return fail(FHMG_EINVAL, "bad arguments");
@@ -1274,7 +1345,7 @@ int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols
 }
 
 int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols, int tile) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "double-float products need a mixed-precision problem");
   if (!X || !Y || ncols < 0 || X == Y || (tile != 0 && tile != 4 && tile != 8 && tile != 16))
     return fail(FHMG_EINVAL, "bad arguments");
@@ -1289,14 +1360,14 @@ int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols,
 }
 
 int fhmg_smooth(fhmg_problem p, double* u, const double* F, int nsweeps) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!u || !F || nsweeps < 0) return fail(FHMG_EINVAL, "bad arguments");
   for (int s = 0; s < nsweeps; ++s) TRY(sweep<double>(p, p->nlev - 1, u, F, K64));
   return FHMG_OK;
 }
 
 int fhmg_residual(fhmg_problem p, const double* u, const double* f, const double* g, double* r) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!u || !r) return fail(FHMG_EINVAL, "bad arrays");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
@@ -1305,21 +1376,21 @@ int fhmg_residual(fhmg_problem p, const double* u, const double* f, const double
 }
 
 int fhmg_restrict_residual(fhmg_problem p, const double* u, const double* F, double* rc) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (p->nlev < 2) return fail(FHMG_EINVAL, "no coarser grid");
   if (!u || !F || !rc) return fail(FHMG_EINVAL, "bad arrays");
   return restrict_defect<double>(p, p->nlev - 1, u, F, rc, K64);
 }
 
 int fhmg_prolong_correct(fhmg_problem p, double* u, const double* e) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (p->nlev < 2) return fail(FHMG_EINVAL, "no coarser grid");
   if (!u || !e) return fail(FHMG_EINVAL, "bad arrays");
   return prolong_add<double>(p, p->nlev - 1, e, u);
 }
 
 int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int nu1, int nu2) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!u || nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0) return fail(FHMG_EINVAL, "bad arguments");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
@@ -1327,7 +1398,7 @@ int fhmg_vcycle(fhmg_problem p, double* u, const double* f, const double* g, int
 }
 
 int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const double* g, double* out) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!u || !out) return fail(FHMG_EINVAL, "bad arguments");
   const double* F;
   TRY(full_rhs(p, f, g, &F));
@@ -1339,7 +1410,7 @@ int fhmg_residual_norm(fhmg_problem p, const double* u, const double* f, const d
 
 int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int nu1, int nu2, double rtol,
                int max_cycles, int* cycles_out, double* relres_out) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!u || nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0 || !(rtol >= 0) || max_cycles < 0)
     return fail(FHMG_EINVAL, "bad arguments");
   const double* F;
@@ -1358,7 +1429,7 @@ int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int 
 
 int fhmg_solve_host(fhmg_problem p, double* u_host, const double* f_host, const double* g_host, int nu1, int nu2,
                     double rtol, int max_cycles, int* cycles_out, double* relres_out) {
-  TRY(check_dims(p));
+  ENTER(p);
   if (!u_host || !f_host) return fail(FHMG_EINVAL, "bad arrays");
   const size_t n = (size_t)p->lev[p->nlev - 1].npts * p->M;
   const size_t ng = (size_t)p->lev[p->nlev - 1].npts;
@@ -1375,6 +1446,22 @@ int fhmg_solve_host(fhmg_problem p, double* u_host, const double* f_host, const 
   return st;
 }
 
+int fhmg_ws_solve_host(fhmg_wsnet net, fhmg_problem p, double* u_host, const double* f_host, double alpha, int K,
+                       int bf16, int nu1, int nu2, double rtol, int max_cycles, int* cycles_out, double* relres_out) {
+  ENTER(p);
+  if (!net || !u_host || !f_host) return fail(FHMG_EINVAL, "bad arguments");
+  const size_t n = (size_t)p->lev[p->nlev - 1].npts * p->M;
+  if (!p->hu) TRY(dalloc(p->allocs, &p->hu, n));
+  if (!p->hf) TRY(dalloc(p->allocs, &p->hf, n));
+  CK(cudaMemcpyAsync(p->hf, f_host, n * sizeof(double), cudaMemcpyHostToDevice, p->st));
+  TRY(fhmg_ws_predict(net, p, p->hf, alpha, K, bf16, p->hu));
+  int st = fhmg_solve(p, p->hu, p->hf, nullptr, nu1, nu2, rtol, max_cycles, cycles_out, relres_out);
+  if (st != FHMG_OK && st != FHMG_ENOTCONV) return st;
+  CK(cudaMemcpyAsync(u_host, p->hu, n * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return st;
+}
+
 int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f, int nu1, int nu2, double rtol,
                        int max_cycles, int* cycles_out, double* relres_out) {
   if (n < 1 || n > 4096 || !probs || !u || !f) return fail(FHMG_EINVAL, "bad batch");
@@ -1382,7 +1469,10 @@ int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f,
   for (int i = 0; i < n; ++i) {
     if (!probs[i] || !u[i] || !f[i]) return fail(FHMG_EINVAL, "null problem or array in the batch");
     if (probs[i]->prec != probs[0]->prec) return fail(FHMG_EINVAL, "all problems of a batch must share the precision");
+    if (probs[i]->dev != probs[0]->dev) return fail(FHMG_EINVAL, "all problems of a batch must be on one device");
   }
+  DeviceScope dev_scope(probs[0]->dev);
+  if (!dev_scope.ok) return fail(FHMG_ECUDA, "cannot make the batch's device current");
   const bool mixed = probs[0]->prec == FHMG_MIXED_FP32;
   const int kind = mixed ? KSPLIT : K64;  // the batched mixed path keeps FP64 storage (valid for every N)
   cudaStream_t st;
@@ -1428,7 +1518,9 @@ int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f,
     std::vector<BLev> sub;
     for (int i : act)
       sub.push_back(mixed ? BLev{probs[i], probs[i]->nlev - 1, probs[i]->Ef, probs[i]->Rs} : set[i]);
-    const int ncyc = mixed ? (probs[0]->inner > 0 ? probs[0]->inner : 4) : 1;
+    // inner cycles of this round, capped so that no instance runs past max_cycles (active
+    // instances advance in lockstep, so they share one count)
+    const int ncyc = std::min(mixed ? (probs[0]->inner > 0 ? probs[0]->inner : 4) : 1, max_cycles - cyc[act[0]]);
     if (mixed)
       for (int i : act)
         CK(cudaMemsetAsync(probs[i]->Ef, 0, sizeof(double) * probs[i]->lev[probs[i]->nlev - 1].npts * probs[i]->M, st));

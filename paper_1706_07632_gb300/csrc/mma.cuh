@@ -144,14 +144,18 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
     if (t != NT) return;
     long long k = 0;
     int slot = 0;
-    bool ok = true;
-    for (long long g = blockIdx.x; g < B.ntiles && ok; g += gridDim.x) {
+    bool ok = true, stop = false;
+    for (long long g = blockIdx.x; g < B.ntiles && ok && !stop; g += gridDim.x) {
       const WalkJob<T, float>& J = B.job[job_of(B, g)];
       const int nch = __ldg(J.P.cptr + J.P.nb);
       int4 cdn = __ldg(J.P.chunks);
       for (int c = 0; c < nch; ++c, ++k) {
         const int4 cd = cdn;
         if (c + 1 < nch) cdn = __ldg(J.P.chunks + c + 1);
+        if (k + 1 == B.withhold) {
+          stop = true;
+          break;
+        }
         if (k >= ns && !mbar_wait_or_abort(empty + slot, (uint32_t)(((k / ns) - 1) & 1), abort_flag)) {
           ok = false;
           break;
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
   auto consumer_sync = [&]() -> bool {
     __syncwarp();
     if (lane == 0) mbar_arrive(cbar);
-    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag);
+    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag, B.spin);
     cbphase ^= 1;
     return !give_up(ok);
   };
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(288) hmma_kernel(const __grid_constant__ WalkB
       load_rhs(i + 1);
       float* xr_i = ring + (size_t)(i % W) * TS;  // x_i tile [column][k]
       for (bool leaf_done = false; !leaf_done;) {
-        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag))) return;
+        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag, B.spin))) return;
         const int4 cd = sdesc[cslot];
         leaf_done = ((cd.x >> 12) & 1) != 0;
         const int type = cd.x & 15, cnt = (cd.x >> 4) & 0xff;

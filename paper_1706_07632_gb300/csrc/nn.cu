@@ -17,13 +17,19 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <random>
 #include <string>
 #include <vector>
 
+#include "devinfo.h"
 #include "fhmg.h"
+
+// Kernel launches issued by this file (network training / inference, warm-start projection and
+// synthesis), reported by fhmg_wsnet_launches.
+static std::atomic<long long> g_nn_launches{0};
 
 int fhmg_internal_fail(int code, const char* msg);
 
@@ -191,10 +197,7 @@ __global__ void to_bf16(long long n, const float* x, __nv_bfloat16* y) {
     y[i] = __float2bfloat16(x[i]);
 }
 
-int nblk(long long n) {
-  long long b = (n + 255) / 256;
-  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
-}
+int nblk(long long n) { return fhmg::grid_for(n, 16); }
 
 }  // namespace
 
@@ -274,6 +277,7 @@ int gemm(cudaStream_t st, int M, int N, int K, float alpha, const float* A, int 
          int tb, float beta, float* C, int ldc, int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0) {
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   gemm_f32<<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, ta, B, ldb, sB, tb, beta, C, ldc, sC);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   return FHMG_OK;
 }
@@ -290,6 +294,7 @@ int forward32(fhmg_wsnet net, cudaStream_t st, const float* X, int n) {
     if ((s = gemm(st, n, wo, wi, 1.f, in, wi, 0, net->P + net->woff[l], wi, 1, 0.f, net->Z[l], wo))) return s;
     bias_act_fwd<<<nblk((long long)n * wo), 256, 0, st>>>(n, wo, net->Z[l], net->P + net->boff[l], net->A[l + 1],
                                                         l < L - 1 ? 1 : 0, nullptr);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
     in = net->A[l + 1];
   }
@@ -301,12 +306,14 @@ int backward32(fhmg_wsnet net, cudaStream_t st, const float* X, const float* Y, 
   const int L = (int)net->width.size() - 1;
   NCK(cudaMemsetAsync(net->loss, 0, sizeof(float), st));
   mse_fwd_bwd<<<nblk(n), 256, 0, st>>>(n, net->A[L], Y, net->dA[L], net->loss);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   for (int l = L - 1; l >= 0; --l) {
     const int wi = net->width[l], wo = net->width[l + 1];
     const float* dz = net->dA[l + 1];
     if (l < L - 1) {
       act_bwd<<<nblk((long long)n * wo), 256, 0, st>>>((long long)n * wo, net->Z[l], net->dA[l + 1], net->dZ);
+      ++g_nn_launches;
       NCK(cudaGetLastError());
       dz = net->dZ;
     }
@@ -315,6 +322,7 @@ int backward32(fhmg_wsnet net, cudaStream_t st, const float* X, const float* Y, 
     int s = gemm(st, wo, wi, n, 1.f, dz, wo, 1, in, wi, 0, 0.f, net->G + net->woff[l], wi);
     if (s) return s;
     colsum<<<(wo + 127) / 128, 128, 0, st>>>(n, wo, dz, net->G + net->boff[l]);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
     if (l > 0 && (s = gemm(st, n, wi, wo, 1.f, dz, wo, 0, net->P + net->woff[l], wi, 0, 0.f, net->dA[l], wi))) return s;
   }
@@ -401,18 +409,22 @@ int fhmg_wsnet_forward(fhmg_wsnet net, const float* X, int n, int bf16, float* Y
   }
   // BF16 tensor-core inference (FP32 accumulation): weights and activations rounded to BF16
   to_bf16<<<nblk(net->nparams), 256, 0, st>>>(net->nparams, net->P, net->Pbf);
+  ++g_nn_launches;
   to_bf16<<<nblk((long long)n * kFeat), 256, 0, st>>>((long long)n * kFeat, X, net->Abf[0]);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   int cur = 0;
   for (int l = 0; l < L; ++l) {
     const int wi = net->width[l], wo = net->width[l + 1];
     dim3 grid((wo + 7) / 8, (n + 63) / 64);
     gemm_bf16_nt<<<grid, 128, 0, st>>>(n, wo, wi, net->Abf[cur], net->Pbf + net->woff[l], net->Z[l]);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
     const bool last = l == L - 1;
     bias_act_fwd<<<nblk((long long)n * wo), 256, 0, st>>>(n, wo, net->Z[l], net->P + net->boff[l],
                                                         last ? Y : nullptr, last ? 0 : 1,
                                                         last ? nullptr : net->Abf[1 - cur]);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
     cur = 1 - cur;
   }
@@ -575,7 +587,9 @@ struct Spectral {
     nm = dim == 1 ? K : K * K;
     if ((s = alloc(&S, (size_t)N * K)) || (s = alloc(&lam, nm)) || (s = alloc(&tdev, M + 1))) return s;
     sine_basis<<<nblk((long long)N * K), 256, 0, st>>>(N, K, S);
+    ++g_nn_launches;
     mode_lambdas<<<(nm + 127) / 128, 128, 0, st>>>(dim, N, Lx, K, nm, lam);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
     NCK(cudaMemcpyAsync(tdev, thost, sizeof(double) * (M + 1), cudaMemcpyHostToDevice, st));
     return FHMG_OK;
@@ -586,10 +600,13 @@ struct Spectral {
     int s = alloc(&S64, (size_t)N * K);
     if (s || (s = alloc(&T, dim == 1 ? (size_t)nl * K : (size_t)nl * K * N))) return s;
     sine_basis64<<<nblk((long long)N * K), 256, 0, st>>>(N, K, S64);
+    ++g_nn_launches;
     const long long na = dim == 1 ? (long long)nl * K : (long long)nl * K * N;
     project64_a<<<nblk(na), 256, 0, st>>>(dim, N, K, nl, x, S64, T);
+    ++g_nn_launches;
     const long long nb_ = dim == 1 ? (long long)nl * K : (long long)nl * K * K;
     project64_b<<<nblk(nb_), 256, 0, st>>>(dim, N, K, nl, T, S64, 2.0 / (N + 1), out);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
     return FHMG_OK;
   }
@@ -612,6 +629,12 @@ struct Spectral {
 
 extern "C" {
 
+int fhmg_wsnet_launches(long long* n) {
+  if (!n) return fhmg_internal_fail(FHMG_EINVAL, "n is NULL");
+  *n = g_nn_launches.load();
+  return FHMG_OK;
+}
+
 int fhmg_ws_predict(fhmg_wsnet net, fhmg_problem prob, const double* f, double alpha, int K, int bf16, double* u0) {
   if (!net || !prob || !f || !u0 || K < 1) return fhmg_internal_fail(FHMG_EINVAL, "bad arguments");
   Spectral sp;
@@ -625,12 +648,15 @@ int fhmg_ws_predict(fhmg_wsnet net, fhmg_problem prob, const double* f, double a
       (s = sp.alloc(&Y, (size_t)nm * M)) || (s = sp.alloc(&G, (size_t)nm * M)))
     return s;
   d2f<<<nblk(npts), 256, 0, sp.st>>>(npts, f + (long long)(M - 1) * npts, f32);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   if ((s = sp.project(f32, 1, c))) return s;
   build_features_kept<<<nblk((long long)nm * M), 256, 0, sp.st>>>(nm, sp.lam, M, sp.tdev, alpha, nullptr, nullptr, X);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   if ((s = fhmg_wsnet_forward(net, X, nm * M, bf16, Y, sp.st))) return s;
   mode_amplitudes<<<nblk((long long)nm * M), 256, 0, sp.st>>>(nm, M, c, Y, sp.lam, G);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   // synthesis u0[m] = sum_k G[m][k] s_k, in FP32, then widened to FP64
   if ((s = sp.alloc(&U, (size_t)M * npts))) return s;
@@ -646,6 +672,7 @@ int fhmg_ws_predict(fhmg_wsnet net, fhmg_problem prob, const double* f, double a
       return s;
   }
   f2d<<<nblk((long long)M * npts), 256, 0, sp.st>>>((long long)M * npts, U, u0);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   NCK(cudaStreamSynchronize(sp.st));
   return FHMG_OK;
@@ -680,7 +707,9 @@ int fhmg_ws_dataset(fhmg_problem prob, const double* u, const double* f, double 
   NCK(cudaMemcpyAsync(dkeep, keep.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, sp.st));
   NCK(cudaMemcpyAsync(dkpos, kpos.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, sp.st));
   build_features_kept<<<nblk((long long)nm * M), 256, 0, sp.st>>>(nm, sp.lam, M, sp.tdev, alpha, dkeep, dkpos, X_out);
+  ++g_nn_launches;
   mode_targets<<<nblk((long long)nm * M), 256, 0, sp.st>>>(nm, M, c, uh, sp.lam, rel_thr, dkeep, dkpos, Y_out);
+  ++g_nn_launches;
   NCK(cudaGetLastError());
   NCK(cudaStreamSynchronize(sp.st));
   *nrows = (long long)nk * M;
@@ -706,6 +735,7 @@ int fhmg_wsnet_train(fhmg_wsnet net, const float* X, const float* Y, long long n
     const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
     adam_step<<<nblk(net->nparams), 256, 0, st>>>(net->nparams, net->P, net->G, net->Mo, net->Vo, lr, b1, b2, c1, c2,
                                                  eps);
+    ++g_nn_launches;
     NCK(cudaGetLastError());
   }
   if (last_loss) {

@@ -7,9 +7,11 @@
 // (the defect at every grid point and the max-norm accumulator) from a file-scope __device__
 // array of fixed size instead of the problem's workspace, and it calls no allocating routine.
 //
-// Set-up: the first call on each device looks up the device address of the array
-// (cudaGetSymbolAddress, with that device current) and caches it; make that first call before
-// any stream capture.
+// Set-up: the first call for a problem on a given device looks up the device address of the array
+// on that device (cudaGetSymbolAddress, with the problem's device made current for the call) and
+// caches it; make that first call before any stream capture.  The cached address belongs to the
+// device's current context: after cudaDeviceReset on that device the module is loaded anew and
+// this entry point must not be called again on that device in the same process.
 //
 // Limits and sharing:
 //  * the defect scratch holds kNoallocMaxElems doubles (16 MiB): problems with
@@ -21,12 +23,15 @@
 //    accumulator is cleared at the start of every call, the defect part is fully overwritten.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "fhmg.h"
 
 struct fhmg_problem_s;
 int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, double* B,
                               unsigned long long* norm_word, double* out);
 long long fhmg_internal_grid_elems(fhmg_problem p);
+int fhmg_internal_problem_device(fhmg_problem p);
 int fhmg_internal_fail(int code, const char* msg);
 
 namespace {
@@ -38,22 +43,41 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocMaxElems + 32];
 
 // Device addresses of the array, resolved once per device (the host-side symbol is only a
-// stand-in and must never be handed to a kernel).
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+// stand-in and must never be handed to a kernel).  Host threads may race on the first lookup;
+// each writes the same address, atomically.
+std::atomic<double*> g_scratch_ptr[kMaxDevices];
 
-int scratch_for_current_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return fhmg_internal_fail(FHMG_ECUDA, "cudaGetDevice failed or device index out of range");
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return fhmg_internal_fail(FHMG_ECUDA, cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+// The array's address on device dev; the caller has made dev current.
+int scratch_for_device(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fhmg_internal_fail(FHMG_ECUDA, "device index out of range");
+  double* ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
+    void* a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess || !a) return fhmg_internal_fail(FHMG_ECUDA, cudaGetErrorString(e));
+    ptr = static_cast<double*>(a);
+    g_scratch_ptr[dev].store(ptr, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = ptr;
   return FHMG_OK;
 }
+
+// Makes dev current for the scope of the call, restoring the caller's device afterwards.
+struct CurrentDevice {
+  int prev = -1;
+  bool ok = false;
+  explicit CurrentDevice(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~CurrentDevice() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 
@@ -63,8 +87,11 @@ extern "C" int fhmg_residual_norm_noalloc(fhmg_problem p, const double* u, const
   if (n > kNoallocMaxElems)
     return fhmg_internal_fail(FHMG_EINVAL,
                               "fhmg_residual_norm_noalloc: M * N^dim exceeds the fixed scratch of 2^21 doubles");
+  const int dev = fhmg_internal_problem_device(p);
+  CurrentDevice scope(dev);
+  if (!scope.ok) return fhmg_internal_fail(FHMG_ECUDA, "cannot make the problem's device current");
   double* scratch = nullptr;
-  int st = scratch_for_current_device(&scratch);
+  int st = scratch_for_device(dev, &scratch);
   if (st != FHMG_OK) return st;
   auto* norm_word = reinterpret_cast<unsigned long long*>(scratch + kNoallocMaxElems);
   return fhmg_internal_defect_norm(p, u, f, scratch, norm_word, out_max);

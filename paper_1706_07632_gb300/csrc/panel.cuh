@@ -150,10 +150,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// bounded wait that also gives up once *abort is set (the producer's waits)
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// bounded wait (limit polls) that also gives up once *abort is set
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                   long long limit = kSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -238,7 +239,10 @@ struct WalkBatch {
   int njobs;
   int ns, pool, W, slot_bytes;
   long long ntiles;  // tiles over all jobs
-  int* err;          // set to 1 if an mbarrier wait exceeds kSpinLimit (the kernel then returns)
+  int* err;          // set to 1 if a bounded mbarrier wait gives up (the kernel then returns)
+  long long spin;    // poll limit of the consumer warps' waits (the producer keeps kSpinLimit)
+  long long withhold;  // > 0: every producer stops before issuing its chunk number withhold - 1
+                       // (test hook: the consumers' waits then run out; nothing else changes)
   WalkJob<T, TM> job[kMaxJobs];
 };
 
@@ -293,14 +297,18 @@ __global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant_
     if (t != NT) return;
     long long k = 0;  // chunks issued
     int slot = 0;
-    bool ok = true;
-    for (long long g = blockIdx.x; g < B.ntiles && ok; g += gridDim.x) {
+    bool ok = true, stop = false;
+    for (long long g = blockIdx.x; g < B.ntiles && ok && !stop; g += gridDim.x) {
       const WalkJob<T, TM>& J = B.job[job_of(B, g)];
       const int nch = __ldg(J.P.cptr + J.P.nb);
       int4 cdn = __ldg(J.P.chunks);
       for (int c = 0; c < nch; ++c, ++k) {
         const int4 cd = cdn;
         if (c + 1 < nch) cdn = __ldg(J.P.chunks + c + 1);
+        if (k + 1 == B.withhold) {
+          stop = true;
+          break;
+        }
         if (k >= ns && !mbar_wait_or_abort(empty + slot, (uint32_t)(((k / ns) - 1) & 1), abort_flag)) {
           ok = false;
           break;
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant_
   auto consumer_sync = [&]() -> bool {
     __syncwarp();
     if (lane == 0) mbar_arrive(cbar);
-    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag);
+    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag, B.spin);
     cbphase ^= 1;
     return !give_up(ok);
   };
@@ -427,7 +435,7 @@ __global__ void __launch_bounds__(NT_ + 32) hpanel_kernel(const __grid_constant_
       }
       TM* xr_i = ring + ((i % W) * TC + cl) * LP;  // x_i of this column, once computed
       for (bool leaf_done = false; !leaf_done;) {
-        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag))) return;
+        if (give_up(mbar_wait_or_abort(full + cslot, cphase, abort_flag, B.spin))) return;
         const int4 cd = sdesc[cslot];
         leaf_done = ((cd.x >> 12) & 1) != 0;
         const int type = cd.x & 15, cnt = (cd.x >> 4) & 0xff;

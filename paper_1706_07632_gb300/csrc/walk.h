@@ -3,25 +3,11 @@
 #pragma once
 #include <string>
 
+#include "devinfo.h"
+
 #include "panel.cuh"
 
 namespace fhmg {
-
-// Raises kern's dynamic shared-memory limit to smem on the current device.  The attribute is held
-// per device, so the limit already set is remembered per device (configured: one entry per device).
-constexpr int kDevSlots = 64;
-template <typename K>
-inline cudaError_t raise_smem_limit(K kern, size_t smem, size_t (&configured)[kDevSlots]) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  size_t& c = configured[dev % kDevSlots];
-  if (smem <= c) return cudaSuccess;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) c = smem;
-  return e;
-}
 
 // One walk job (one instance).
 template <typename T>
@@ -41,6 +27,8 @@ struct WalkArgsT {
   int tile;                    // 0: automatic, else the column tile TC (the first job's is used)
   PanelDev PM;                 // FP32 products only: the stream in the tensor-core layout (pkg NULL: none)
   const void* DinvM;           // and the level inverses in that layout
+  long long spin;              // consumer-side poll limit of the bounded waits (0: kSpinLimit; first job's)
+  long long withhold;          // test hook, 0: off; else the producers withhold chunk withhold - 1 (first job's)
 };
 using WalkArgs = WalkArgsT<double>;
 

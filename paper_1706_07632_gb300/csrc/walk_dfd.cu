@@ -20,7 +20,7 @@ int df_launch_t(cudaStream_t st, WalkBatch<double, float>& B, std::string* err) 
   // the ring for two CTAs per SM (16 consumer warps hide the latency of the double-float chains
   // better than a deeper ring: 3.9 vs 5.3 ms for 4095 columns x M = 4096); else the deepest ring
   const size_t other = df_smem(L, TC, B.pool, B.W, B.slot_bytes, 0).total + 64;
-  const size_t budget = (TC <= 8 && B.ntiles > 152) ? kDfSmemMax / 2 - 1024 : kDfSmemMax;
+  const size_t budget = (TC <= 8 && B.ntiles > device_sms()) ? kDfSmemMax / 2 - 1024 : kDfSmemMax;
   int ns = other < budget ? (int)((budget - other) / (size_t)B.slot_bytes) : 0;
   ns = std::min(ns, 8);
   if (ns < 2 && budget < kDfSmemMax)
@@ -31,18 +31,17 @@ int df_launch_t(cudaStream_t st, WalkBatch<double, float>& B, std::string* err) 
   }
   B.ns = ns;
   const size_t smem = df_smem(L, TC, B.pool, B.W, B.slot_bytes, ns).total;
-  static size_t configured[kDevSlots] = {};
+  static KernelCache cache;
+  int occ = 1;
   {
-    cudaError_t e = raise_smem_limit(kern, smem, configured);
+    cudaError_t e = prepare_launch(kern, kDfBlock, smem, cache, &occ);
     if (e != cudaSuccess) {
-      *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+      *err = std::string("double-float walk set-up: ") + cudaGetErrorString(e);
       return 1;
     }
   }
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDfBlock, smem) != cudaSuccess || occ < 1) occ = 1;
   if (B.ntiles <= 0) return 0;
-  const long long grid = std::min<long long>(B.ntiles, 152LL * occ);
+  const long long grid = std::min<long long>(B.ntiles, (long long)device_sms() * occ);
   kern<<<(unsigned)grid, kDfBlock, smem, st>>>(B);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -67,6 +66,8 @@ int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs
   B.W = 1;
   B.slot_bytes = 16;
   B.err = jobs[0].err;
+  B.spin = jobs[0].spin > 0 ? jobs[0].spin : kSpinLimit;
+  B.withhold = jobs[0].withhold;
   long long cols = 0;
   for (int j = 0; j < njobs; ++j) {
     if (jobs[j].P.L != L || jobs[j].mode != mode || (mode == MODE_SMOOTH && jobs[j].geo.dim != 0)) {
@@ -80,7 +81,7 @@ int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs
   }
   // column tile: 8 once the columns give every SM a tile of 8 (two CTAs per SM), else 4
   int TC = jobs[0].tile;
-  if (TC != 1 && TC != 4 && TC != 8 && TC != 16) TC = cols >= 8LL * 152 ? 8 : cols >= 4LL * 152 ? 4 : 1;
+  if (TC != 1 && TC != 4 && TC != 8 && TC != 16) TC = cols >= 8LL * device_sms() ? 8 : cols >= 4LL * device_sms() ? 4 : 1;
   bool per_column = false;
   for (int j = 0; j < njobs; ++j) per_column |= jobs[j].dinv_cstride != 0;
   if (per_column) TC = 1;  // each column streams its own inverses

@@ -8,7 +8,6 @@
 
 namespace fhmg {
 
-constexpr int kPanelSMs = 152;
 constexpr int kPanelThreads = 256;                  // consumer threads of the walk
 constexpr int kPanelBlock = kPanelThreads + 32;     // + the producer warp
 constexpr size_t kPanelSmemCap = 200 * 1024;
@@ -27,24 +26,17 @@ template <typename T, typename TM, int L, int TC, int MODE>
 int panel_launch_t(cudaStream_t st, const WalkBatch<T, TM>& B, std::string* err) {
   auto kern = hpanel_kernel<T, TM, L, TC, MODE, kPanelThreads>;
   const size_t smem = panel_bytes<T, TM>(L, TC, B.pool, B.W, B.slot_bytes, B.ns);
-  static size_t configured[kDevSlots] = {};
-  static size_t occ_smem = 0;
-  static int occ = 1;
+  static KernelCache cache;
+  int occ = 1;
   {
-    cudaError_t e = raise_smem_limit(kern, smem, configured);
+    cudaError_t e = prepare_launch(kern, kPanelBlock, smem, cache, &occ);
     if (e != cudaSuccess) {
-      *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+      *err = std::string("panel launch set-up: ") + cudaGetErrorString(e);
       return 1;
     }
   }
-  if (occ_smem != smem) {
-    int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPanelBlock, smem) != cudaSuccess || o < 1) o = 1;
-    occ = o;
-    occ_smem = smem;
-  }
   if (B.ntiles <= 0) return 0;
-  const long long grid = std::min<long long>(B.ntiles, (long long)kPanelSMs * occ);
+  const long long grid = std::min<long long>(B.ntiles, (long long)device_sms() * occ);
   kern<<<(unsigned)grid, kPanelBlock, smem, st>>>(B);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -58,10 +50,10 @@ int panel_launch_t(cudaStream_t st, const WalkBatch<T, TM>& B, std::string* err)
 // staged chunk for all TC columns), TC = 1 when there are fewer columns than SMs; shrunk until
 // the shared-memory layout fits.
 template <typename T, typename TM>
-int panel_pick(int L, int pool, int W, int slot_bytes, int ns, long long ncols) {
+int panel_pick(int L, int pool, int W, int slot_bytes, int ns, long long ncols, int sms) {
   const int tcmax = (L == 64 && sizeof(TM) == 8) ? 16 : 32;  // FP64 leaf-64 tiles of 32 spill
   int tc = 1;
-  while (tc < tcmax && (ncols + 2 * tc - 1) / (2 * tc) >= kPanelSMs) tc *= 2;
+  while (tc < tcmax && (ncols + 2 * tc - 1) / (2 * tc) >= sms) tc *= 2;
   while (tc > 1 && panel_bytes<T, TM>(L, tc, pool, W, slot_bytes, ns) > kPanelSmemCap) tc /= 2;
   return tc;
 }
@@ -73,6 +65,7 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
     return 2;
   }
   const int L = jobs[0].P.L;
+  const int sms = device_sms();
   int pool = 0, W = 1, slot = 16;
   long long cols = 0;
   for (int j = 0; j < njobs; ++j) {
@@ -101,7 +94,7 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
       mma_ok = mma_ok && jobs[j].PM.pkg != nullptr && !jobs[j].PM.far && jobs[j].dinv_cstride == 0;
     if (mma_ok) {
       int tcm = jobs[0].tile;
-      if (tcm == 0) tcm = total_cols >= 32LL * kPanelSMs ? 32 : total_cols >= 2048 ? 16 : 0;
+      if (tcm == 0) tcm = total_cols >= 32LL * sms ? 32 : total_cols >= 2048 ? 16 : 0;
       if (tcm == 16 || tcm == 32) {
         if (tile_used) *tile_used = tcm;
         WalkBatch<T, float> Bm;
@@ -110,6 +103,8 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
         Bm.W = 1;
         Bm.slot_bytes = 16;
         Bm.err = jobs[0].err;
+        Bm.spin = jobs[0].spin > 0 ? jobs[0].spin : kSpinLimit;
+        Bm.withhold = jobs[0].withhold;
         long long tiles = 0;
         for (int j = 0; j < njobs; ++j) {
           Bm.pool = std::max(Bm.pool, jobs[j].PM.pool);
@@ -139,14 +134,14 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
   for (int j = 0; j < njobs; ++j) per_column_inverse |= jobs[j].dinv_cstride != 0;
   const int TC = per_column_inverse ? 1
                  : jobs[0].tile     ? jobs[0].tile
-                                    : panel_pick<T, TM>(L, pool, W, slot, ns, total_cols);
+                                    : panel_pick<T, TM>(L, pool, W, slot, ns, total_cols, sms);
   if (tile_used) *tile_used = TC;
   // Pipeline depth: when every tile gets its own SM (one CTA per SM), a CTA has little work per
   // chunk and the copies' latency dominates -- deepen the ring up to ~200 KB of shared memory;
   // otherwise keep ~96 KB of slots so that two CTAs fit per SM.
   long long tiles_all = 0;
   for (int j = 0; j < njobs; ++j) tiles_all += (jobs[j].ncols + TC - 1) / TC;
-  if (tiles_all <= kPanelSMs) {
+  if (tiles_all <= sms) {
     const size_t other = panel_bytes<T, TM>(L, TC, pool, W, slot, 0);
     while (ns < 16 && other + (size_t)(ns + 1) * slot + 64 <= kPanelSmemCap) ++ns;
   }
@@ -161,6 +156,8 @@ int panel_dispatch(cudaStream_t st, const WalkArgsT<T>* jobs, int njobs, std::st
   B.W = W;
   B.slot_bytes = slot;
   B.err = jobs[0].err;
+  B.spin = jobs[0].spin > 0 ? jobs[0].spin : kSpinLimit;
+  B.withhold = jobs[0].withhold;
   long long tiles = 0;
   for (int j = 0; j < njobs; ++j) {
     WalkJob<T, TM>& J = B.job[j];

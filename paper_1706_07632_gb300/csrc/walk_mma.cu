@@ -24,18 +24,17 @@ int mma_launch_t(cudaStream_t st, WalkBatch<T, float>& B, std::string* err) {
   }
   B.ns = ns;
   const size_t smem = mma_smem(TC, B.pool, B.W, B.slot_bytes, ns).total;
-  static size_t configured[kDevSlots] = {};
+  static KernelCache cache;
+  int occ = 1;
   {
-    cudaError_t e = raise_smem_limit(kern, smem, configured);
+    cudaError_t e = prepare_launch(kern, kMmaBlock, smem, cache, &occ);
     if (e != cudaSuccess) {
-      *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+      *err = std::string("tensor-core walk set-up: ") + cudaGetErrorString(e);
       return 1;
     }
   }
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kMmaBlock, smem) != cudaSuccess || occ < 1) occ = 1;
   if (B.ntiles <= 0) return 0;
-  const long long grid = std::min<long long>(B.ntiles, 152LL * occ);
+  const long long grid = std::min<long long>(B.ntiles, (long long)device_sms() * occ);
   kern<<<(unsigned)grid, kMmaBlock, smem, st>>>(B);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -53,7 +53,11 @@ enum fhmg_status {
 
 enum fhmg_prec {
   FHMG_FP64 = 0,       /* every product in FP64 */
-  FHMG_MIXED_FP32 = 1  /* defect correction: FP64 residual, FP32 inner V-cycles */
+  FHMG_MIXED_FP32 = 1, /* defect correction: FP64 residual, FP32 inner V-cycles */
+  FHMG_MIXED_BF16 = 2  /* as FHMG_MIXED_FP32, but the inner cycles' FP32-storage walks over panels wide
+                          enough for a 128-column tile per SM run BF16 H-matrix products with FP32
+                          accumulation on the tcgen05 tensor cores (leaf 64; narrower walks and the
+                          FP64-storage levels keep the FP32 products) */
 };
 
 const char* fhmg_last_error(void);
@@ -130,6 +134,14 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols);
  * enabled (fhmg_problem_set_tensor_cores) tiles 16 and 32 run on the tensor cores. */
 int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, long long ncols, int tile);
 int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols, int tile);
+/* The FP32-storage walks of the mixed path's inner cycles on FP32 device arrays [M][ncols]
+ * (mixed-precision problems only): X = (R~ + s_level I)^{-1} B (Algorithm 4; X may alias B) and
+ * Y = R~ X (Algorithm 3; Y must not alias X).  FHMG_MIXED_BF16 problems run them on the tcgen05 walk
+ * when ncols >= 128 x the SM count: BF16 products (H-matrix entries, x, y and z operands rounded to
+ * BF16) with FP32 accumulation; the diagonal of the diagonal leaves (and of the level inverses) is
+ * applied in FP32.  Otherwise FP32 products (3xTF32 tensor cores or SIMT). */
+int fhmg_line_solve_s(fhmg_problem p, int level, float* X, const float* B, long long ncols);
+int fhmg_hmatvec_s(fhmg_problem p, float* Y, const float* X, long long ncols);
 /* Y = R~ X with the double-float products of fhmg_problem_set_defect_arith (mixed-precision
  * problems only; EINVAL otherwise); device [M][ncols] FP64; tile 0 (automatic), 4, 8 or 16. */
 int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols, int tile);

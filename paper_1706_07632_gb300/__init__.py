@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfhmg.so")
 
 FHMG_OK, FHMG_EINVAL, FHMG_ECUDA, FHMG_ENOMEM, FHMG_ENOTCONV, FHMG_ENAN, FHMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-FP64, MIXED_FP32 = 0, 1
+FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 _STATUS = {0: "FHMG_OK", -1: "FHMG_EINVAL", -2: "FHMG_ECUDA", -3: "FHMG_ENOMEM", -4: "FHMG_ENOTCONV",
            -5: "FHMG_ENAN", -6: "FHMG_ETIMEOUT"}
 
@@ -48,6 +48,8 @@ _SIGS = {
     "fhmg_hmatvec": (_I, [_P, _P, _P, _LL]),
     "fhmg_line_solve_f32": (_I, [_P, _I, _P, _P, _LL, _I]),
     "fhmg_hmatvec_f32": (_I, [_P, _P, _P, _LL, _I]),
+    "fhmg_line_solve_s": (_I, [_P, _I, _P, _P, _LL]),
+    "fhmg_hmatvec_s": (_I, [_P, _P, _P, _LL]),
     "fhmg_smooth": (_I, [_P, _P, _P, _I]),
     "fhmg_residual": (_I, [_P, _P, _P, _P, _P]),
     "fhmg_restrict_residual": (_I, [_P, _P, _P, _P]),
@@ -249,6 +251,14 @@ class Problem:
 
     def hmatvec_f32(self, Y, X, tile=0):
         _check(lib().fhmg_hmatvec_f32(self._p, _ptr(Y), _ptr(X), X.numel() // self.M, tile))
+
+    def line_solve_s(self, level, X, B):
+        """FP32-storage line solve (float32 tensors); BF16 problems: tcgen05 walk on wide panels."""
+        _check(lib().fhmg_line_solve_s(self._p, level, _fptr(X), _fptr(B), B.numel() // self.M))
+
+    def hmatvec_s(self, Y, X):
+        """FP32-storage product Y = R~ X (float32 tensors)."""
+        _check(lib().fhmg_hmatvec_s(self._p, _fptr(Y), _fptr(X), X.numel() // self.M))
 
     def smooth(self, u, F, nsweeps=1):
         _check(lib().fhmg_smooth(self._p, _ptr(u), _ptr(F), nsweeps))

@@ -71,6 +71,7 @@ struct LevelData {
   double* Dinv64 = nullptr;    // (D_ii + s I)^{-1}, FP64, in the chunk layout (to_panel_layout)
   float* Dinv32 = nullptr;     // the same in FP32 without its diagonal (mixed path)
   float* Dinv32m = nullptr;    // ... and as TF32 hi/lo pairs in the tensor-core layout (to_mma_layout)
+  uint16_t* Dinv32u = nullptr; // ... and as BF16 in the tcgen05 layout (to_umma_layout; BF16 problems)
   double* dinvdiag = nullptr;  // the inverses' diagonal, FP64 (mixed path) ...
   float* dinvdiag32 = nullptr; // ... and FP32 (FP32 inner cycles)
 };
@@ -88,6 +89,7 @@ struct fhmg_problem_s {
   DevPanel panel32;  // chunk stream, FP32 matrices (mixed path)
   DevPanel panel32m; // the same in the tensor-core layout (build_panel_mma)
   DevPanel panel64df; // FP64-accurate products in double-float arithmetic (build_panel_df)
+  DevPanel panel32u;  // BF16 products on tcgen05 for the FP32-storage walks (build_panel_umma; BF16 problems)
   int defect_df = 1;  // mixed path: the outer FP64 defect's products in double-float arithmetic
   int use_mma = 1;   // FP32 products on the tensor cores where the column tile allows
   double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path) ...
@@ -153,10 +155,13 @@ int upload(std::vector<void*>& list, const std::vector<S>& src, const T** out, s
 }
 
 // Uploads the chunk stream of the H-matrix (elem_bytes 8: FP64 products, 4: FP32 products,
-// 0: FP32 products in the tensor-core layout, -1: FP64-accurate double-float products).
+// 0: FP32 products in the tensor-core layout, -1: FP64-accurate double-float products, -2: BF16
+// products in the tcgen05 layout).
 int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, DevPanel& D) {
   fhmg::PanelHost ph;
-  if (elem_bytes == 0)
+  if (elem_bytes == -2)
+    fhmg::build_panel_umma(h, f, ph);
+  else if (elem_bytes == 0)
     fhmg::build_panel_mma(h, f, ph);
   else if (elem_bytes < 0)
     fhmg::build_panel_df(h, f, ph);
@@ -280,6 +285,10 @@ fhmg::WalkArgsT<T> smooth_job(fhmg_problem p, int l, int kind, const Geo& g, lon
   a.norm = nullptr;
   a.err = p->derr;
   a.tile = tuned_tile(p, kind, fhmg::MODE_SMOOTH, nc);
+  if (kind == K32 && p->panel32u.d.pkg) {
+    a.PU = p->panel32u.d;
+    a.DinvU = lv.Dinv32u;
+  }
   return a;
 }
 
@@ -301,6 +310,7 @@ fhmg::WalkArgsT<T> matvec_job(fhmg_problem p, int kind, long long nc, const T* X
   a.norm = norm;
   a.err = p->derr;
   a.tile = tuned_tile(p, kind, fhmg::MODE_MATVEC, nc);
+  if (kind == K32 && p->panel32u.d.pkg) a.PU = p->panel32u.d;
   return a;
 }
 
@@ -328,11 +338,16 @@ int launch_jobs(cudaStream_t st, int kind, std::vector<fhmg::WalkArgsT<double>>&
   return FHMG_OK;
 }
 
+// FP32-storage walks: BF16 problems run wide panels (every SM gets a 128-column tile) on the
+// tcgen05 walk, everything else on the FP32-product walks.
 int launch_jobs(cudaStream_t st, int, std::vector<fhmg::WalkArgsT<float>>& jobs, long long* counter) {
   for (auto& j : jobs) {
     if (j.ncols <= 0) continue;
     std::string err;
-    TRY(walk_status(fhmg::walk_launch_ff(st, &j, 1, &err, nullptr), err));
+    int s = 2;
+    if (j.PU.pkg && j.ncols >= 128LL * fhmg::device_sms()) s = fhmg::walk_launch_umma(st, &j, 1, &err);
+    if (s == 2) s = fhmg::walk_launch_ff(st, &j, 1, &err, nullptr);
+    TRY(walk_status(s, err));
     if (counter) ++*counter;
   }
   return FHMG_OK;
@@ -539,7 +554,7 @@ int read_norm(fhmg_problem p, double* out) {
 // Products of the FP64 defect on the finest grid: double-float for mixed problems (unless set
 // to FP64 by fhmg_problem_set_defect_arith), FP64 otherwise.
 int defect_kind(fhmg_problem p) {
-  return (p->prec == FHMG_MIXED_FP32 && p->defect_df && p->panel64df.d.pkg) ? KDF : K64;
+  return (p->prec != FHMG_FP64 && p->defect_df && p->panel64df.d.pkg) ? KDF : K64;
 }
 
 // FP64 defect on the finest grid.  colour0_only (after a completed red-black sweep the defect
@@ -971,6 +986,7 @@ int fhmg_problem_destroy(fhmg_problem p) {
   for (void* a : p->panel32.allocs) cudaFree(a);
   for (void* a : p->panel32m.allocs) cudaFree(a);
   for (void* a : p->panel64df.allocs) cudaFree(a);
+  for (void* a : p->panel32u.allocs) cudaFree(a);
   delete p;
   return FHMG_OK;
 }
@@ -980,7 +996,8 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
   if (dim != 1 && dim != 2) return fail(FHMG_EINVAL, "dim must be 1 or 2");
   if (N < 1 || ((N + 1) & N) != 0) return fail(FHMG_EINVAL, "N must be 2^levels - 1 (got %d)", N);
   if (!(Lx > 0)) return fail(FHMG_EINVAL, "Lx must be > 0");
-  if (prec != FHMG_FP64 && prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "unknown precision %d", prec);
+  if (prec != FHMG_FP64 && prec != FHMG_MIXED_FP32 && prec != FHMG_MIXED_BF16)
+    return fail(FHMG_EINVAL, "unknown precision %d", prec);
   fhmg_problem p = new (std::nothrow) fhmg_problem_s;
   if (!p) return fail(FHMG_ENOMEM, "host allocation failed");
   p->H = h;
@@ -1005,9 +1022,11 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     fhmg_problem_destroy(p);
     return s;
   };
-  const bool mixed = prec == FHMG_MIXED_FP32;
+  const bool mixed = prec != FHMG_FP64;
+  const bool umma = prec == FHMG_MIXED_BF16 && p->L == fhmg::kUmmaL;
   if ((st = upload_panel(h->host, h->flat, 8, p->panel64)) != FHMG_OK) return bail(st);
   if (mixed) {
+    if (umma && (st = upload_panel(h->host, h->flat, -2, p->panel32u)) != FHMG_OK) return bail(st);
     if ((st = upload_panel(h->host, h->flat, 4, p->panel32)) != FHMG_OK) return bail(st);
     if (p->L == 64 && (st = upload_panel(h->host, h->flat, 0, p->panel32m)) != FHMG_OK) return bail(st);
     if ((st = upload_panel(h->host, h->flat, -1, p->panel64df)) != FHMG_OK) return bail(st);
@@ -1051,6 +1070,15 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
       const float* dd32;
       if ((st = upload(p->allocs, dg, &dd32, nullptr)) != FHMG_OK) return bail(st);
       lv.dinvdiag32 = const_cast<float*>(dd32);
+      if (umma) {
+        std::vector<uint16_t> u(inv.size());
+        for (int i = 0; i < p->nb; ++i) fhmg::to_umma_layout(&inv[i * LL], p->L, true, &u[i * LL]);
+        uint16_t* du;
+        if ((st = dalloc(p->allocs, &du, u.size())) != FHMG_OK) return bail(st);
+        if (cudaMemcpy(du, u.data(), u.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+          return bail(fail(FHMG_ECUDA, "cudaMemcpy failed"));
+        lv.Dinv32u = du;
+      }
       if (p->L == 64) {
         std::vector<float> m(inv.size() * 2);
         for (int i = 0; i < p->nb; ++i) fhmg::to_mma_layout(&inv[i * LL], p->L, true, &m[i * LL * 2]);
@@ -1104,7 +1132,7 @@ int fhmg_problem_autotune(fhmg_problem p) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   std::vector<int> kinds{K64};
-  if (p->prec == FHMG_MIXED_FP32) kinds.push_back(KSPLIT);
+  if (p->prec != FHMG_FP64) kinds.push_back(KSPLIT);
   int st = FHMG_OK;
   auto time_jobs = [&](int kind, fhmg::WalkArgsT<double> job, float* ms) -> int {
     std::vector<fhmg::WalkArgsT<double>> v{job};
@@ -1219,7 +1247,7 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   TRY(upload(p->dallocs, tw, &dtw, nullptr));
   p->dTw = reinterpret_cast<double2*>(const_cast<double*>(dtw));
   TRY(dalloc(p->dallocs, &p->dModeInv, (size_t)lv.npts * nb * L * L));
-  if (p->prec == FHMG_MIXED_FP32 && p->panel64df.d.pkg)
+  if (p->prec != FHMG_FP64 && p->panel64df.d.pkg)
     TRY(dalloc(p->dallocs, &p->dModeInvDF, (size_t)lv.npts * nb * 2 * L * L));
   TRY(dalloc(p->dallocs, &p->dCA, (size_t)lv.npts * p->M));
   TRY(dalloc(p->dallocs, &p->dCB, (size_t)lv.npts * p->M));
@@ -1319,7 +1347,7 @@ int fhmg_hmatvec(fhmg_problem p, double* Y, const double* X, long long ncols) {
 
 int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, long long ncols, int tile) {
   ENTER(p);
-  if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
+  if (p->prec == FHMG_FP64) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
   if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
   if (!X || !B || ncols < 0 || tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
     return fail(FHMG_EINVAL, "bad arguments");
@@ -1331,7 +1359,7 @@ int fhmg_line_solve_f32(fhmg_problem p, int level, double* X, const double* B, l
 
 int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols, int tile) {
   ENTER(p);
-  if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
+  if (p->prec == FHMG_FP64) return fail(FHMG_EINVAL, "FP32 products need a mixed-precision problem");
   if (!X || !Y || ncols < 0 || X == Y || tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
     return fail(FHMG_EINVAL, "bad arguments");
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
@@ -1346,7 +1374,7 @@ int fhmg_hmatvec_f32(fhmg_problem p, double* Y, const double* X, long long ncols
 
 int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols, int tile) {
   ENTER(p);
-  if (p->prec != FHMG_MIXED_FP32) return fail(FHMG_EINVAL, "double-float products need a mixed-precision problem");
+  if (p->prec == FHMG_FP64) return fail(FHMG_EINVAL, "double-float products need a mixed-precision problem");
   if (!X || !Y || ncols < 0 || X == Y || (tile != 0 && tile != 4 && tile != 8 && tile != 16))
     return fail(FHMG_EINVAL, "bad arguments");
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * ncols * p->M, p->st));
@@ -1354,6 +1382,32 @@ int fhmg_hmatvec_df(fhmg_problem p, double* Y, const double* X, long long ncols,
   j[0].tile = tile;
   TRY(launch_jobs(p->st, KDF, j, &p->launches));
   scale_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M, -1.0);
+  ++p->launches;
+  CK(cudaGetLastError());
+  return FHMG_OK;
+}
+
+int fhmg_line_solve_s(fhmg_problem p, int level, float* X, const float* B, long long ncols) {
+  ENTER(p);
+  if (p->prec == FHMG_FP64) return fail(FHMG_EINVAL, "FP32-storage walks need a mixed-precision problem");
+  if (level < 0 || level >= p->nlev) return fail(FHMG_EINVAL, "level out of range");
+  if (!X || !B || ncols < 0) return fail(FHMG_EINVAL, "bad arrays");
+  Geo g{0, 0, 0, ncols, 0.0};
+  return walk_smooth<float>(p, level, K32, g, ncols, X, B);
+}
+
+__global__ void negate_float_kernel(float* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = -y[i];
+}
+
+int fhmg_hmatvec_s(fhmg_problem p, float* Y, const float* X, long long ncols) {
+  ENTER(p);
+  if (p->prec == FHMG_FP64) return fail(FHMG_EINVAL, "FP32-storage walks need a mixed-precision problem");
+  if (!X || !Y || ncols < 0 || X == Y) return fail(FHMG_EINVAL, "bad arrays");
+  CK(cudaMemsetAsync(Y, 0, sizeof(float) * ncols * p->M, p->st));
+  TRY(walk_matvec<float>(p, K32, ncols, X, Y, Y, nullptr));
+  negate_float_kernel<<<blocks_for(ncols * p->M), 256, 0, p->st>>>(Y, ncols * p->M);
   ++p->launches;
   CK(cudaGetLastError());
   return FHMG_OK;
@@ -1417,7 +1471,7 @@ int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int 
   TRY(full_rhs(p, f, g, &F));
   int k = 0;
   double r0 = 0, r = 0;
-  if (p->prec == FHMG_MIXED_FP32)
+  if (p->prec != FHMG_FP64)
     TRY(solve_mixed(p, u, F, nu1, nu2, rtol, max_cycles, &k, &r0, &r));
   else
     TRY(solve_fp64(p, u, F, nu1, nu2, rtol, max_cycles, &k, &r0, &r));
@@ -1473,7 +1527,7 @@ int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f,
   }
   DeviceScope dev_scope(probs[0]->dev);
   if (!dev_scope.ok) return fail(FHMG_ECUDA, "cannot make the batch's device current");
-  const bool mixed = probs[0]->prec == FHMG_MIXED_FP32;
+  const bool mixed = probs[0]->prec != FHMG_FP64;
   const int kind = mixed ? KSPLIT : K64;  // the batched mixed path keeps FP64 storage (valid for every N)
   cudaStream_t st;
   CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -1594,7 +1648,7 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
     // time one V-cycle (after a warm-up cycle) on the zeroed workspace: iterate and right-hand
     // side both in Rs (fine-grid size; values do not change the cost)
     const LevelData& fine = p->lev[p->nlev - 1];
-    const int kind = p->prec == FHMG_MIXED_FP32 ? KSPLIT : K64;
+    const int kind = p->prec != FHMG_FP64 ? KSPLIT : K64;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms = 0.f;
     if (s == FHMG_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {

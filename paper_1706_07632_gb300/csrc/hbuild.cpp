@@ -729,6 +729,96 @@ void build_panel_df(const HostH& h, const FlatH& f, PanelHost& out) {
   }
 }
 
+namespace {
+
+// BF16 bits of v, round to nearest even (finite values)
+uint16_t bf16_bits(double v) {
+  const float x = (float)v;
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7f800000u) != 0x7f800000u) b += 0x7fffu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+
+}  // namespace
+
+size_t umma_offset(int r, int k, int K) {
+  return ((size_t)(r / 8) * (K / 8) + k / 8) * 128 + (size_t)(r % 8) * 16 + (size_t)(k % 8) * 2;
+}
+
+void build_panel_umma(const HostH& h, const FlatH& f, PanelHost& out) {
+  const int L = f.L, nb = f.nb;
+  out = PanelHost();
+  out.cptr.assign(nb + 1, 0);
+  int maxdist = 0;
+  for (int i = 0; i < nb; ++i)
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) maxdist = std::max(maxdist, i - f.dlist_col[d]);
+  out.W = std::min(8, maxdist + 1);
+  out.far = maxdist + 1 > out.W;
+  auto add_chunk = [&](int type, int count, int aux, size_t bytes) -> size_t {
+    size_t off = out.pkg.size();
+    size_t nbytes = pad16(bytes);
+    out.pkg.resize(off + nbytes, 0);
+    out.chunks.push_back(type | (count << 4));
+    out.chunks.push_back(aux);
+    out.chunks.push_back((int)nbytes);
+    out.chunks.push_back((int)(off / 16));
+    out.slot_bytes = std::max(out.slot_bytes, (int)nbytes);
+    return off;
+  };
+  auto put = [&](size_t off, int r, int k, int K, double v) {
+    const uint16_t b = bf16_bits(v);
+    std::memcpy(&out.pkg[off + umma_offset(r, k, K)], &b, 2);
+  };
+  for (int i = 0; i < nb; ++i) {
+    for (int d = f.dptr[i]; d < f.dptr[i + 1]; ++d) {
+      const double* D = &f.dense_data[(size_t)f.dlist_blk[d] * L * L];
+      size_t off = add_chunk(CH_DENSE, L, f.dlist_col[d], (size_t)L * L * 2);
+      for (int r = 0; r < L; ++r)
+        for (int k = 0; k < L; ++k) put(off, r, k, L, D[(size_t)r * L + k]);
+    }
+    const int K = f.uptr[i + 1] - f.uptr[i];
+    for (int k0 = 0; k0 < K; k0 += L) {
+      const int kc = std::min(L, K - k0);
+      const int kp = (kc + 15) / 16 * 16;
+      const size_t mat = (size_t)L * kp * 2;
+      size_t off = add_chunk(CH_UPART, kp, k0, mat + (size_t)kp * 4);
+      for (int r = 0; r < L; ++r)
+        for (int kk = 0; kk < kc; ++kk) put(off, r, kk, kp, f.udata[f.uoff[i] + (size_t)r * K + k0 + kk]);
+      for (int kk = 0; kk < kp; ++kk) {
+        int z = f.uz[f.uptr[i] + k0 + (kk < kc ? kk : 0)];
+        std::memcpy(&out.pkg[off + mat + (size_t)kk * 4], &z, 4);
+      }
+    }
+    {
+      const double* D = &f.dense_data[(size_t)f.diag_blk[i] * L * L];
+      size_t off = add_chunk(CH_DIAG, L, i, (size_t)L * L * 2);
+      for (int r = 0; r < L; ++r)
+        for (int k = 0; k < L; ++k) put(off, r, k, L, k == r ? 0.0 : D[(size_t)r * L + k]);
+    }
+    const int Kv = f.vptr[i + 1] - f.vptr[i];
+    for (int k0 = 0; k0 < Kv; k0 += L) {
+      const int kc = std::min(L, Kv - k0);
+      const int rp = (kc + 15) / 16 * 16;
+      const size_t mat = (size_t)rp * L * 2;
+      size_t off = add_chunk(CH_VPART, kc, k0, mat + (size_t)kc * 4);
+      for (int kk = 0; kk < kc; ++kk)
+        for (int c = 0; c < L; ++c) put(off, kk, c, L, f.vdata[f.voff[i] + (size_t)(k0 + kk) * L + c]);
+      for (int kk = 0; kk < kc; ++kk) {
+        int code = 2 * f.vz[f.vptr[i] + k0 + kk] + f.vinit[f.vptr[i] + k0 + kk];
+        std::memcpy(&out.pkg[off + mat + (size_t)kk * 4], &code, 4);
+      }
+    }
+    out.chunks[out.chunks.size() - 4] |= 1 << 12;
+    out.cptr[i + 1] = (int)(out.chunks.size() / 4);
+  }
+}
+
+void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out) {
+  for (int r = 0; r < L; ++r)
+    for (int k = 0; k < L; ++k) out[umma_offset(r, k, L) / 2] = bf16_bits((zero_diag && k == r) ? 0.0 : A[(size_t)r * L + k]);
+}
+
 void to_mma_layout(const double* A, int L, bool zero_diag, float* out) {
   const int nkb = (L + 15) / 16;
   std::vector<unsigned char> buf((size_t)nkb * 16 * nkb * 16 * 2 * 4, 0);

@@ -8,6 +8,7 @@
 // block tree into per-leaf-row panels that the CUDA kernels walk in time order.
 #pragma once
 #include <cstddef>
+#include <cstdint>
 #include <vector>
 
 namespace fhmg {
@@ -117,6 +118,20 @@ void to_mma_layout(const double* A, int L, bool zero_diag, float* out);
 // layout, then the chunk's int indices.  DIAG blocks keep their diagonal (products only).
 void build_panel_df(const HostH& h, const FlatH& f, PanelHost& out);
 
+
+// The same stream for the tcgen05 walk (BF16 products, FP32 accumulation in tensor memory): every
+// chunk matrix is the B operand of tcgen05.mma kind::f16, R rows (the outputs) by K (the reduction
+// index), K-major in the canonical layout without swizzle: 8 x 8 core matrices of 128 contiguous
+// bytes (row-major, 16 bytes per row), entry (r, k) at byte umma_offset(r, k, K) =
+// ((r/8) (K/8) + k/8) 128 + (r%8) 16 + (k%8) 2, so that adjacent core matrices along K are 128 bytes
+// apart (the descriptor's leading byte offset) and adjacent row groups (K/8) 128 bytes apart (its
+// stride byte offset).  DENSE: R = K = L; UPART: R = L, K = count padded to 16 (padding columns zero,
+// their z indices the slab's first), then the K z indices; DIAG: D_ii without its diagonal (applied
+// in FP32 by the kernel); VPART: R = count padded to 16 (zero rows), K = L, then count codes.
+void build_panel_umma(const HostH& h, const FlatH& f, PanelHost& out);
+size_t umma_offset(int r, int k, int K);
+// The row-major L x L matrix A in that layout (BF16 bits, L*L values), optionally without its diagonal.
+void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out);
 
 // Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
 // Returns 0 on success, < 0 on invalid arguments.

@@ -27,6 +27,8 @@ struct WalkArgsT {
   int tile;                    // 0: automatic, else the column tile TC (the first job's is used)
   PanelDev PM;                 // FP32 products only: the stream in the tensor-core layout (pkg NULL: none)
   const void* DinvM;           // and the level inverses in that layout
+  PanelDev PU;                 // FP32-storage walks of BF16 problems: the tcgen05 stream (pkg NULL: none)
+  const void* DinvU;           // and the level inverses in that layout
   long long spin;              // consumer-side poll limit of the bounded waits (0: kSpinLimit; first job's)
   long long withhold;          // test hook, 0: off; else the producers withhold chunk withhold - 1 (first job's)
 };
@@ -42,6 +44,11 @@ int walk_launch_ff(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std
 // on compact columns (MODE_SMOOTH, geo.dim 0; Dinv: inverses as float pairs, 2 L^2 floats per leaf,
 // dinv_cstride floats per column); the jobs' P is the build_panel_df stream; tile 1, 4, 8 or 16
 // (0: automatic; 1 whenever columns have their own inverses).
+// tcgen05 walks (BF16 products, FP32 storage, leaf 64, 128-column tiles), walk_umma.cu: the jobs' PU
+// stream and DinvU inverses.  Returns 2 (no kernel) if a job lacks them or needs far near-field blocks.
+int walk_launch_umma(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std::string* err);
+constexpr int kUmmaL = 64;  // leaf size of the tcgen05 walk
+
 int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 
 // Tensor-core walks (FP32 products, leaf 64, TC 16 or 32), walk_mma.cu.  B.ns is chosen here.

@@ -131,12 +131,17 @@ __device__ __forceinline__ void put8(unsigned char* tile, int c, int k0, int K, 
   *reinterpret_cast<uint4*>(tile + umma_off(c, k0, K)) = q;
 }
 
+// row c of a K-major operand tile: entries k0..k0+7 already packed as BF16 pairs
+__device__ __forceinline__ void put8_packed(unsigned char* tile, int c, int k0, int K, const uint32_t* q) {
+  *reinterpret_cast<uint4*>(tile + umma_off(c, k0, K)) = make_uint4(q[0], q[1], q[2], q[3]);
+}
+
 // T = float grid functions; the jobs' Dinv are the level inverses (without diagonal) in the
 // build_panel_umma layout (BF16 bits), ddiag the diagonal applied in FP32.
 template <int MODE>
-__global__ void __launch_bounds__(kUmmaBlock, 2) humma_kernel(const __grid_constant__ WalkBatch<float, uint16_t> B) {
+__global__ void __maxnreg__(200) humma_kernel(const __grid_constant__ WalkBatch<float, uint16_t> B) {
   constexpr int L = kUmmaL, NT = kUmmaCols;
-  extern __shared__ __align__(128) unsigned char sm[];
+  extern __shared__ __align__(16) unsigned char sm[];
   const UmmaSmem lay = umma_smem(B.pool, B.W, B.slot_bytes, B.ns);
   unsigned char* slots = sm;
   unsigned char* ring = sm + lay.ring;
@@ -242,6 +247,16 @@ __global__ void __launch_bounds__(kUmmaBlock, 2) humma_kernel(const __grid_const
   };
   // all consumer warps meet (bounded); tensor-memory reads and shared writes before it are ordered
   // before the MMAs issued after it
+  // arrive_wait: the same meeting without the fences, for callers that fenced already and issued
+  // global loads since (a proxy fence would wait for those loads to complete)
+  auto arrive_wait = [&]() -> bool {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(cbar);
+    const bool ok = mbar_wait_or_abort(cbar, cbphase, abort_flag, B.spin);
+    cbphase ^= 1;
+    tc_after_sync();
+    return !give_up(ok);
+  };
   auto consumer_sync = [&]() -> bool {
     async_proxy_fence();
     tc_before_sync();
@@ -286,33 +301,69 @@ __global__ void __launch_bounds__(kUmmaBlock, 2) humma_kernel(const __grid_const
       }
     }
     double local_max = 0.0;
-    for (int i = 0; i < nb && !failed; ++i) {
-      // right-hand side of the leaf (smoother: F + neighbour sum / h^2), x_i (product)
-      float b[L], xv[MODE == MODE_MATVEC ? L : 1];
+    // right-hand side of a leaf (smoother: F + neighbour sum / h^2) and, for the product, its x;
+    // loaded one leaf ahead (issued right after the previous leaf's diagonal step, the last use of
+    // these registers), so the loads overlap that leaf's V products and this leaf's first MMAs.
+    // Rows of leaf i + 1 are never written during leaf i (X, OUT alias B only row by row).
+    // b: right-hand side (product: B - d_rr x, the diagonal term folded in at load time);
+    // xq: the product's x_i as packed BF16 pairs for the ring
+    float b[L];
+    uint32_t xq[MODE == MODE_MATVEC ? L / 2 : 1];
+    // columns past the panel's end read column 0 (any valid address) and are zeroed, so that the
+    // loads carry no predicate; compact columns load their 64 values as independent loads, grid
+    // columns in groups of 8 rows (5 loads per row: the point and its neighbours), which bounds
+    // the registers the loads in flight hold
+    const long long pa = valid ? p : 0;
+    const float keep = valid ? 1.f : 0.f;
+    const bool grid = MODE == MODE_SMOOTH && J.geo.dim > 0;
+    auto load_leaf = [&](int leaf) {
+      if (leaf >= nb) return;
+      const float* Bl = Bsrc + (long long)leaf * L * ld + pa;
+      if (!grid) {
 #pragma unroll
-      for (int r = 0; r < L; ++r) {
-        float v = 0.f;
-        if (valid) {
-          const long long base = (long long)(i * L + r) * ld;
-          v = Bsrc[base + p];
-          if (MODE == MODE_SMOOTH) {
-            float s = 0.f;
+        for (int r = 0; r < L; ++r) b[r] = Bl[(long long)r * ld] * keep;
+        if (MODE == MODE_MATVEC) {
+          const float* Xl = X + (long long)leaf * L * ld + pa;
+          const float* dd = ddg + (long long)leaf * L;
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (nbr[e] >= 0) s += X[base + nbr[e]];
-            v += s * inv_h2;
+          for (int r = 0; r < L; r += 2) {
+            const float x0 = Xl[(long long)r * ld] * keep, x1 = Xl[(long long)(r + 1) * ld] * keep;
+            b[r] -= __ldg(dd + r) * x0;
+            b[r + 1] -= __ldg(dd + r + 1) * x1;
+            xq[r / 2] = pack_bf16(x0, x1);
           }
         }
-        b[r] = v;
+        return;
       }
+      const float* Xl = X + (long long)leaf * L * ld;
+      const long long n0 = nbr[0] >= 0 ? nbr[0] : pa, n1 = nbr[1] >= 0 ? nbr[1] : pa;
+      const long long n2 = nbr[2] >= 0 ? nbr[2] : pa, n3 = nbr[3] >= 0 ? nbr[3] : pa;
+      const float w0 = nbr[0] >= 0 ? inv_h2 : 0.f, w1 = nbr[1] >= 0 ? inv_h2 : 0.f;
+      const float w2 = nbr[2] >= 0 ? inv_h2 : 0.f, w3 = nbr[3] >= 0 ? inv_h2 : 0.f;
+#pragma unroll
+      for (int r0 = 0; r0 < L; r0 += 8) {
+        float v[8], a0[8], a1[8], a2[8], a3[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const long long o = (long long)(r0 + j) * ld;
+          v[j] = Bl[o];
+          a0[j] = Xl[o + n0];
+          a1[j] = Xl[o + n1];
+          a2[j] = Xl[o + n2];
+          a3[j] = Xl[o + n3];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[r0 + j] = keep * (v[j] + w0 * a0[j] + w1 * a1[j] + w2 * a2[j] + w3 * a3[j]);
+      }
+    };
+    load_leaf(0);
+    for (int i = 0; i < nb && !failed; ++i) {
       unsigned char* xr_i = ring + (size_t)(i % W) * tile_bytes;
       if (MODE == MODE_MATVEC) {
         // x_i into the ring now (its slot's previous tile, x_{i-W}, was last read by leaf i-1's MMAs,
         // complete since this thread waited on their barriers)
 #pragma unroll
-        for (int r = 0; r < L; ++r) xv[r] = valid ? X[(long long)(i * L + r) * ld + p] : 0.f;
-#pragma unroll
-        for (int r = 0; r < L; r += 8) put8(xr_i, c, r, L, &xv[r]);
+        for (int r = 0; r < L; r += 8) put8_packed(xr_i, c, r, L, &xq[r / 2]);
       }
       bool acc_used = false;
       int nu = 0;  // UPART chunks of this leaf so far
@@ -397,15 +448,19 @@ __global__ void __launch_bounds__(kUmmaBlock, 2) humma_kernel(const __grid_const
               float a[16];
               tmem_ld16(t_res + lane_base + r0, a);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const float x = a[j] + __ldg(dd + r0 + j) * b[r0 + j];
-                a[j] = x;
-                if (valid) X[(long long)(i * L + r0 + j) * ld + p] = x;
-              }
-              put8(xr_i, c, r0, L, a);
-              put8(xr_i, c, r0 + 8, L, a + 8);
+              for (int j = 0; j < 16; ++j) b[r0 + j] = a[j] + __ldg(dd + r0 + j) * b[r0 + j];  // b := x_i
+              put8(xr_i, c, r0, L, &b[r0]);
+              put8(xr_i, c, r0 + 8, L, &b[r0 + 8]);
             }
-            if (!consumer_sync()) {  // x_i complete in the ring before the V products read it
+            async_proxy_fence();  // x_i in the ring, ordered before the V products ...
+            tc_before_sync();     // ... and the reads of res before later MMAs
+            // global stores and loads only after the fence, which would otherwise wait for them
+            if (valid) {
+#pragma unroll
+              for (int r = 0; r < L; ++r) X[(long long)(i * L + r) * ld + p] = b[r];
+            }
+            load_leaf(i + 1);
+            if (!arrive_wait()) {  // x_i complete in the ring before the V products read it
               failed = true;
               break;
             }
@@ -423,14 +478,13 @@ __global__ void __launch_bounds__(kUmmaBlock, 2) humma_kernel(const __grid_const
               failed = true;
               break;
             }
-            const float* dd = ddg + (long long)i * L;
 #pragma unroll
             for (int r0 = 0; r0 < L; r0 += 16) {
               float a[16];
               tmem_ld16(t_acc + lane_base + r0, a);
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
-                const float o = b[r0 + j] - a[j] - __ldg(dd + r0 + j) * xv[r0 + j];
+                const float o = b[r0 + j] - a[j];
                 if (valid) {
                   if (J.OUT) J.OUT[(long long)(i * L + r0 + j) * ld + p] = o;
                   const double av = fabs((double)o);
@@ -438,7 +492,9 @@ __global__ void __launch_bounds__(kUmmaBlock, 2) humma_kernel(const __grid_const
                 }
               }
             }
-            if (!consumer_sync()) {  // every thread has read acc before the next leaf's MMAs
+            tc_before_sync();  // the reads of acc ordered before the next leaf's MMAs
+            load_leaf(i + 1);
+            if (!arrive_wait()) {  // every thread has read acc before the next leaf's MMAs
               failed = true;
               break;
             }

@@ -19,7 +19,8 @@ int umma_launch_t(cudaStream_t st, WalkBatch<float, uint16_t>& B, std::string* e
   // slots fit beside the operand tiles, else one CTA with the deepest ring that fits
   const size_t other = umma_smem(B.pool, B.W, B.slot_bytes, 0).total + 128;
   int ns = other < kUmmaTwoPerSM ? (int)((kUmmaTwoPerSM - other) / (size_t)B.slot_bytes) : 0;
-  if (ns < 3) ns = other < kUmmaSmemMax ? (int)((kUmmaSmemMax - other) / (size_t)B.slot_bytes) : 0;
+  const bool two = ns >= 3;
+  if (!two) ns = other < kUmmaSmemMax ? (int)((kUmmaSmemMax - other) / (size_t)B.slot_bytes) : 0;
   ns = std::min(ns, 12);
   if (ns < 2) {
     *err = "tcgen05 walk: no room for two chunk slots in shared memory";
@@ -37,8 +38,12 @@ int umma_launch_t(cudaStream_t st, WalkBatch<float, uint16_t>& B, std::string* e
     }
   }
   if (B.ntiles <= 0) return 0;
-  // at most two resident CTAs per SM: each allocates half of the SM's tensor memory
-  const long long grid = std::min<long long>(B.ntiles, (long long)device_sms() * std::min(occ, 2));
+  // two CTAs per SM when the shared memory was planned for two (each allocates half of the SM's
+  // tensor memory; the registers of __launch_bounds__(.., 2) allow it), else one.  Persistent CTAs
+  // never wait on one another, so a CTA that finds no room simply starts when another one ends.
+  const long long per_sm = two ? 2 : 1;
+  (void)occ;
+  const long long grid = std::min<long long>(B.ntiles, (long long)device_sms() * per_sm);
   kern<<<(unsigned)grid, kUmmaBlock, smem, st>>>(B);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -8,15 +8,16 @@ constant in time; V(1,1) cycles until the max-norm defect is <= 1e-8 max|F| (the
 target for every initial guess); the coarse-grid correction on the 31^2 level is solved exactly.
 One step = one complete warm-started solve: the network's prediction of the initial iterate
 (projection, BF16 inference, synthesis) and the mixed-precision solve from it (defect correction:
-FP64-accurate double-float outer defects around V-cycles with FP32 storage and 3xTF32
-tensor-core H-matrix products).
+FP64-accurate double-float outer defects around V-cycles with FP32 storage whose H-matrix products
+run in BF16 on the tcgen05 tensor cores with FP32 accumulation in tensor memory).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
 
 value     = DOF * K_ref * ranks / (device time per step), DOF = N^2 M, K_ref = the FP64 path's V(1,1)
             cycle count on the headline source: every arm is expressed in FP64-cycle equivalents,
-            so values compare time to solution.  Arms beside it: plain FP64 from zero and mixed
-            from zero, each the median of >= 5 timed solves; err_vs_oracle of every arm at 4096
+            so values compare time to solution.  Arms beside it: plain FP64 from zero, mixed (BF16
+            products) from zero, each the median of >= 5 timed solves, and the mixed form with FP32
+            products (3xTF32 mma.sync) from zero (median of 3); err_vs_oracle of every arm at 4096
             sampled grid points against the per-mode oracle.
 sources   = 16 unseen GRF sources with alpha ~ U[.3, .8]: cycles and time from zero and from the
             warm start, and the error against the per-mode oracle, per source.
@@ -261,21 +262,22 @@ def events():
 
 
 def train_net(fh, stream):
-    """The warm-start network, trained on library solves (N=255^2, M=512, 8 alphas, sources with
-    seeds 200..207 -- none of them used below)."""
+    """The warm-start network, trained on library solves (N=255^2, M=512, 11 alphas, sources with
+    seeds 200..210 -- none of them used below)."""
     import torch
     from paper_1706_07632_gb300 import warmstart
-    alphas = [0.3, 0.37, 0.44, 0.51, 0.58, 0.65, 0.72, 0.8]
+    alphas = [0.3 + 0.05 * k for k in range(11)]
     t0 = time.perf_counter()
-    X, Y = warmstart.generate(2, 255, HEAD["M"], HEAD["gamma"], alphas, seeds=list(range(200, 208)), K=HEAD["K"])
+    X, Y = warmstart.generate(2, 255, HEAD["M"], HEAD["gamma"], alphas, seeds=list(range(200, 211)), K=HEAD["K"])
     t_data = time.perf_counter() - t0
     net = fh.WSNet(320, 3, seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = warmstart.train(net, X, Y, steps=3000, batch=4096, lr=2e-3)
+    losses = warmstart.train(net, X, Y, steps=4500, batch=4096, lr=2e-3)
     torch.cuda.synchronize()
     return net, {"samples": int(X.shape[0]), "data_s": t_data, "train_s": time.perf_counter() - t0,
-                 "loss": losses[-1], "params": net.num_params(), "train_grid": "N=255^2, M=512, 8 alphas, seeds 200-207"}
+                 "loss": losses[-1], "params": net.num_params(),
+                 "train_grid": "N=255^2, M=512, 11 alphas 0.30..0.80, seeds 200-210, 4500 Adam steps"}
 
 
 def problem(fh, H, prec, stream, tune):
@@ -314,7 +316,7 @@ def measure_headline(fh, a, stream, dist):
     t_hbuild = time.perf_counter() - t0
     t, _ = H.mesh()
     f = warmstart.source_field(2, h["seed"], t[1:], h["N"])
-    Pm = problem(fh, H, fh.MIXED_FP32, stream, not a.no_autotune)
+    Pm = problem(fh, H, fh.MIXED_BF16, stream, not a.no_autotune)
     u = torch.zeros_like(f)
     rtol = a.rtol
 
@@ -359,6 +361,14 @@ def measure_headline(fh, a, stream, dist):
     ts, (k, rr) = timed(lambda: zero_solve(Pm), stream, 5)
     arms["mixed_zero"] = {"time_to_rtol_s": statistics.median(ts), "times_s": ts, "cycles": k, "relres_vs_maxF": rr,
                           "err_vs_oracle": sampled_err(u, ref, iy, ix)}
+    # the mixed form with FP32 products (3xTF32 mma.sync walks), from zero
+    Pf = problem(fh, H, fh.MIXED_FP32, stream, not a.no_autotune)
+    zero_solve(Pf)
+    ts, (k, rr) = timed(lambda: zero_solve(Pf), stream, 3)
+    arms["mixed_fp32_zero"] = {"time_to_rtol_s": statistics.median(ts), "times_s": ts, "cycles": k,
+                               "relres_vs_maxF": rr, "err_vs_oracle": sampled_err(u, ref, iy, ix)}
+    del Pf
+    torch.cuda.empty_cache()
     # e2e: the warm-started solve from pinned host buffers through fhmg_ws_solve_host
     f_host = f.cpu().pin_memory()
     u_host = torch.empty(f.shape, dtype=torch.float64).pin_memory()
@@ -399,7 +409,7 @@ def measure_sources(fh, net_holder, a, stream):
         H = fh.HMatrix(alpha, h["gamma"], 1.0, h["M"], 64, 0, 1e-10)
         t, _ = H.mesh()
         f = warmstart.source_field(2, seed, t[1:], h["N"])
-        P = problem(fh, H, fh.MIXED_FP32, stream, False)
+        P = problem(fh, H, fh.MIXED_BF16, stream, False)
         u = torch.zeros_like(f)
 
         def zero():
@@ -454,7 +464,7 @@ def measure_manufactured(fh, stream, dim, N, M, alpha, gamma, nc, steps, tune):
     w = direct.solve_o2_mode(R, lam, amp)
     ref = torch.as_tensor(w, device=dev).reshape((-1,) + (1,) * dim) * torch.as_tensor(s, device=dev)[None]
     out = {}
-    for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32)):
+    for name, prec in (("fp64", fh.FP64), ("mixed", fh.MIXED_FP32), ("mixed_bf16", fh.MIXED_BF16)):
         P = fh.Problem(H, dim, N, 1.0, prec, stream)
         P.set_coarse_direct(nc)
         if tune:
@@ -477,8 +487,9 @@ def measure_manufactured(fh, stream, dim, N, M, alpha, gamma, nc, steps, tune):
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_rtol_s"] / out["mixed"]["time_to_rtol_s"]
     k_ref = out["fp64"]["cycles"]
     dof = N ** dim * M
-    for name in ("fp64", "mixed"):
+    for name in ("fp64", "mixed", "mixed_bf16"):
         out[name]["dof_cycles_per_s"] = dof * k_ref / out[name]["time_to_rtol_s"]
+    out["speedup_mixed_bf16_vs_fp64"] = out["fp64"]["time_to_rtol_s"] / out["mixed_bf16"]["time_to_rtol_s"]
     return out
 
 
@@ -546,20 +557,19 @@ def measure_batched(fh, stream, rtol, n_inst=64, seed=7):
 
 
 def roofline_smoother(H, cnt, ms_total, ncols, M, hbm_peak, bf16_peak, peak_kind):
-    """Finest-grid smoother half-sweeps of the mixed path (FP32 storage, 3xTF32 tensor-core
-    products), timed live.  Algorithmic HBM bytes per column: the column's right-hand side, the
-    neighbours' values (each value of the other colour once) and the column written, 4 bytes each
-    per time level (12 M bytes); algorithmic tensor work: 3 TF32 products per FP32-accurate
-    flop.  The bound is whichever takes longer at its peak."""
+    """Finest-grid smoother half-sweeps of the mixed path (FP32 storage, BF16 products on the
+    tcgen05 tensor cores), timed live.  Algorithmic HBM bytes per column: the column's right-hand
+    side, the neighbours' values (each value of the other colour once) and the column written, 4
+    bytes each per time level (12 M bytes); algorithmic tensor work: the H-matrix flops of one
+    walk.  The bound is whichever takes longer at its peak."""
     n = max(cnt["smooth_launches"], 1)
     t = cnt["smooth_ms"] / n / 1e3
     bytes_launch = 12.0 * M * ncols
     flops_launch = H.flops_per_column() * ncols
-    tf32_peak = bf16_peak / 2.0
     t_hbm = bytes_launch / (hbm_peak * 1e9)
-    t_tc = 3.0 * flops_launch / (tf32_peak * 1e12)
+    t_tc = flops_launch / (bf16_peak * 1e12)
     tr = TRAFFIC_PER_COLUMN.get("smooth")
-    common = {"kernel": "hmma_kernel<float,32,SMOOTH> (finest-grid half-sweep, FP32 storage, 3xTF32 mma.sync)",
+    common = {"kernel": "humma_kernel<SMOOTH> (finest-grid half-sweep, FP32 storage, BF16 tcgen05.mma, TMEM accumulators)",
               "avg_launch_ms": t * 1e3, "launches_timed": cnt["smooth_launches"],
               "share_of_step": cnt["smooth_ms"] / ms_total if ms_total > 0 else None,
               "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
@@ -568,9 +578,9 @@ def roofline_smoother(H, cnt, ms_total, ncols, M, hbm_peak, bf16_peak, peak_kind
         ach = bytes_launch / t / 1e9
         return dict(common, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
                     peak_note=f"copy bandwidth, {peak_kind}")
-    ach = 3.0 * flops_launch / t / 1e12
-    return dict(common, bound="tensor", achieved=ach, peak=tf32_peak, unit="TFLOP/s", frac=ach / tf32_peak,
-                peak_note=f"TF32 = BF16 dense ({peak_kind}) / 2")
+    ach = flops_launch / t / 1e12
+    return dict(common, bound="tensor", achieved=ach, peak=bf16_peak, unit="TFLOP/s", frac=ach / bf16_peak,
+                peak_note=f"BF16 dense, {peak_kind}")
 
 
 def roofline_defect(H, cnt, ms_total, ncols):
@@ -646,11 +656,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DOF*cycles/s", "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": hd["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
                 "config": head_config(a.rtol, not a.no_autotune),
                 "headline": ("mixed precision + learned warm start: network prediction of u0, then defect correction "
                              "with double-float FP64-accurate outer defects around V-cycles with FP32 storage and "
-                             "3xTF32 tensor-core H-matrix products"),
+                             "BF16 H-matrix products on the tcgen05 tensor cores (FP32 accumulation in tensor memory)"),
                 "cycle_unit": f"FP64 V(1,1) cycles to the target on the headline source = {k_ref}",
                 "arms": arms,
                 "speedup_mixed_warm_vs_fp64": arms["fp64_zero"]["time_to_rtol_s"] / arms["mixed_warm"]["time_to_rtol_s"],

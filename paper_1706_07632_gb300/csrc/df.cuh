@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
             for (int a = 0; a < 4; ++a) ph[q][a] = pl[q][a] = 0.f;
           }
           if (!consumer_sync()) return;  // y is complete
-#pragma unroll
+#pragma unroll 2  // full unrolling overflows the instruction cache
           for (int gg = 0; gg < NVT; ++gg) {
             const int g = sp + gg * S;
             const float4 vh = *reinterpret_cast<const float4*>(yh + g * VE);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
           }
           const bool far = type == PK_DENSE && i - cd.y >= W;
           const double* xj = X + (long long)cd.y * L * ld + p;
-#pragma unroll
+#pragma unroll 2  // full unrolling overflows the instruction cache
           for (int gg = 0; gg < NVT; ++gg) {
             const int g = sp + gg * S;
             float4 vh, vl;
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
           const float4* Al = Ah + L * cnt / 4;
           const int* uz = reinterpret_cast<const int*>(buf + (size_t)cnt * L * 8);
           const int nvq = cnt / VE;
-#pragma unroll
+#pragma unroll 2  // full unrolling overflows the instruction cache
           for (int gg = 0; gg < NVT; ++gg) {
             const int g = sp + gg * S;
             if (g < nvq) {
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(288) hdf_kernel(const __grid_constant__ WalkBa
             const bool live = act && r < cnt;
             float zh[4] = {0, 0, 0, 0}, zl[4] = {0, 0, 0, 0};
             if (live) {
-#pragma unroll
+#pragma unroll 2
               for (int gg = 0; gg < NVT; ++gg) {
                 const int g = sp + gg * S;
                 df_vec(zh, zl, Ah[g * cnt + r], Al[g * cnt + r], *reinterpret_cast<const float4*>(xh + g * VE),

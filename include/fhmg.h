@@ -85,6 +85,15 @@ int fhmg_hmatrix_dense(fhmg_hmatrix h, double* R_out);
 /* Algorithmic FP64 flops of one H-matvec (Algorithm 3) or line solve (Algorithm 4) per column. */
 int fhmg_hmatrix_flops(fhmg_hmatrix h, double* flops_per_column);
 int fhmg_hmatrix_destroy(fhmg_hmatrix h);
+/* Two-grid convergence factor predicted by mode analysis (Section 5, the SAMA column of Table 2):
+ * sine modes in space (a mode and its partner N+1-k per dimension: 2x2 groups in 1D, 4x4 in 2D),
+ * the time matrix exactly -- on each group every time block is a rational function of the
+ * lower-triangular time matrix, so the two-grid operator's eigenvalues are those of the group
+ * matrices at the diagonal entries R_mm.  Two-grid cycle with nu1 pre- and nu2 post-smoothing
+ * red-black sweeps (nu1 + nu2 >= 1), full weighting, (bi)linear interpolation, exact coarse solve, on
+ * the dim-D grid of N = 2^k - 1 >= 3 points per dimension of (0, Lx).  Host computation; *rho_out
+ * receives the largest spectral radius over the paired modes k (and l) = 1..(N-1)/2 and all m. */
+int fhmg_sama_two_grid(fhmg_hmatrix h, int dim, int N, double Lx, int nu1, int nu2, double* rho_out);
 
 /* Creates a problem on the current CUDA device: dim in {1,2}; N = 2^levels - 1 interior points
  * per dimension (levels >= 1); Lx > 0 domain length; prec an fhmg_prec; stream a cudaStream_t

@@ -36,6 +36,7 @@ _SIGS = {
     "fhmg_hmatrix_dense": (_I, [_P, _P]),
     "fhmg_hmatrix_flops": (_I, [_P, _c.POINTER(_D)]),
     "fhmg_hmatrix_destroy": (_I, [_P]),
+    "fhmg_sama_two_grid": (_I, [_P, _I, _I, _D, _I, _I, _c.POINTER(_D)]),
     "fhmg_problem_create": (_I, [_P, _I, _I, _D, _I, _P, _c.POINTER(_P)]),
     "fhmg_problem_destroy": (_I, [_P]),
     "fhmg_problem_autotune": (_I, [_P]),
@@ -163,6 +164,12 @@ class HMatrix:
     def flops_per_column(self):
         v = _D()
         _check(lib().fhmg_hmatrix_flops(self._h, ctypes.byref(v)))
+        return v.value
+
+    def sama_two_grid(self, dim, N, Lx=1.0, nu1=0, nu2=1):
+        """Two-grid convergence factor predicted by mode analysis (fhmg_sama_two_grid)."""
+        v = _D()
+        _check(lib().fhmg_sama_two_grid(self._h, dim, N, Lx, nu1, nu2, ctypes.byref(v)))
         return v.value
 
     def __del__(self):

@@ -971,6 +971,19 @@ int fhmg_hmatrix_flops(fhmg_hmatrix h, double* flops_per_column) {
   return FHMG_OK;
 }
 
+int fhmg_sama_two_grid(fhmg_hmatrix h, int dim, int N, double Lx, int nu1, int nu2, double* rho_out) {
+  if (!h || !rho_out) return fail(FHMG_EINVAL, "null argument");
+  if (dim != 1 && dim != 2) return fail(FHMG_EINVAL, "dim must be 1 or 2");
+  if (N < 3 || ((N + 1) & N) != 0) return fail(FHMG_EINVAL, "N must be 2^levels - 1 >= 3 (got %d)", N);
+  if (!(Lx > 0) || nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0) return fail(FHMG_EINVAL, "bad arguments");
+  const int L = h->host.L;
+  std::vector<double> rdiag((size_t)h->host.M);
+  for (int i = 0; i < h->host.nb; ++i)
+    for (int r = 0; r < L; ++r) rdiag[(size_t)i * L + r] = h->host.dense[h->host.diag[i]].D[(size_t)r * L + r];
+  *rho_out = fhmg::sama_two_grid(rdiag, dim, N, Lx / (N + 1), nu1, nu2);
+  return FHMG_OK;
+}
+
 int fhmg_hmatrix_destroy(fhmg_hmatrix h) {
   delete h;
   return FHMG_OK;

@@ -133,6 +133,10 @@ size_t umma_offset(int r, int k, int K);
 // The row-major L x L matrix A in that layout (BF16 bits, L*L values), optionally without its diagonal.
 void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out);
 
+// Two-grid convergence factor by mode analysis (sama.cpp): the largest spectral radius of the
+// per-mode-group two-grid matrices with the time matrix replaced by its diagonal entries rdiag.
+double sama_two_grid(const std::vector<double>& rdiag, int dim, int N, double h, int nu1, int nu2);
+
 // Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
 // Returns 0 on success, < 0 on invalid arguments.
 int build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,

@@ -75,6 +75,13 @@ const char* fhmg_last_error(void);
  * On success *out owns host memory released by fhmg_hmatrix_destroy. */
 int fhmg_build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,
                        fhmg_hmatrix* out);
+/* The same H-matrix with its low-rank blocks built algebraically (the construction Section 6 names
+ * for kernels without a separable expansion): each admissible block by adaptive cross approximation
+ * with partial pivoting from single accurate entries R_{m,j} (pivot row -> its largest residual
+ * entry's column -> the next pivot row at the column's largest unused residual entry), stopped at
+ * |u_k| |v_k| <= 0.01 tol |sum u_l v_l^T|_F, then recompressed (QR + SVD) to singular values
+ * > tol * (largest of the block) like the Taylor form.  tol > 0; the other arguments as above. */
+int fhmg_build_hmatrix_aca(double alpha, double gamma, double T, int M, int leaf, double tol, fhmg_hmatrix* out);
 /* Block counts, largest rank and bytes of the FP64 device representation. Any pointer may be NULL. */
 int fhmg_hmatrix_info(fhmg_hmatrix h, int* n_dense, int* n_lowrank, int* max_rank, size_t* bytes);
 /* Copies the mesh t_0..t_M (M+1 host doubles) and the initial-data weights d_{m,m} (M host

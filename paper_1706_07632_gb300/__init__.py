@@ -31,6 +31,7 @@ _LL = _c.c_longlong
 _SIGS = {
     "fhmg_last_error": (_c.c_char_p, []),
     "fhmg_build_hmatrix": (_I, [_D, _D, _D, _I, _I, _I, _D, _c.POINTER(_P)]),
+    "fhmg_build_hmatrix_aca": (_I, [_D, _D, _D, _I, _I, _D, _c.POINTER(_P)]),
     "fhmg_hmatrix_info": (_I, [_P, _c.POINTER(_I), _c.POINTER(_I), _c.POINTER(_I), _c.POINTER(_c.c_size_t)]),
     "fhmg_hmatrix_mesh": (_I, [_P, _P, _P]),
     "fhmg_hmatrix_dense": (_I, [_P, _P]),
@@ -136,9 +137,14 @@ def _stream_ptr(stream):
 class HMatrix:
     """fhmg_build_hmatrix: mesh, L1 matrix and its H-matrix form (host, one-time)."""
 
-    def __init__(self, alpha, gamma, T, M, leaf=64, rank=0, tol=1e-10):
+    def __init__(self, alpha, gamma, T, M, leaf=64, rank=0, tol=1e-10, lowrank="taylor"):
+        """lowrank "taylor": the paper's kernel expansion (Section 3); "aca": built algebraically by
+        adaptive cross approximation (needs rank 0 and tol > 0)."""
         h = _P()
-        _check(lib().fhmg_build_hmatrix(alpha, gamma, T, M, leaf, rank, tol, ctypes.byref(h)))
+        if lowrank == "aca":
+            _check(lib().fhmg_build_hmatrix_aca(alpha, gamma, T, M, leaf, tol, ctypes.byref(h)))
+        else:
+            _check(lib().fhmg_build_hmatrix(alpha, gamma, T, M, leaf, rank, tol, ctypes.byref(h)))
         self._h = h
         self.alpha, self.gamma, self.T, self.M = alpha, gamma, T, M
         self.leaf, self.rank, self.tol = leaf, rank, tol

@@ -931,6 +931,22 @@ int fhmg_build_hmatrix(double alpha, double gamma, double T, int M, int leaf, in
   return FHMG_OK;
 }
 
+int fhmg_build_hmatrix_aca(double alpha, double gamma, double T, int M, int leaf, double tol, fhmg_hmatrix* out) {
+  if (!out) return fail(FHMG_EINVAL, "out is NULL");
+  if (!(tol > 0.0)) return fail(FHMG_EINVAL, "tol must be > 0");
+  const int L = std::min(leaf, M);
+  if (!(L == 16 || L == 32 || L == 64)) return fail(FHMG_EINVAL, "leaf size min(leaf, M) = %d not in {16,32,64}", L);
+  fhmg_hmatrix h = new (std::nothrow) fhmg_hmatrix_s;
+  if (!h) return fail(FHMG_ENOMEM, "host allocation failed");
+  if (fhmg::build_hmatrix(alpha, gamma, T, M, leaf, 0, tol, h->host, 1) != 0) {
+    delete h;
+    return fail(FHMG_EINVAL, "invalid arguments: need 0<alpha<1, gamma>=1, T>0, M = leaf*2^p, tol>0");
+  }
+  fhmg::flatten(h->host, h->flat);
+  *out = h;
+  return FHMG_OK;
+}
+
 int fhmg_hmatrix_info(fhmg_hmatrix h, int* n_dense, int* n_lowrank, int* max_rank, size_t* bytes) {
   if (!h) return fail(FHMG_EINVAL, "null hmatrix");
   if (n_dense) *n_dense = (int)h->host.dense.size();

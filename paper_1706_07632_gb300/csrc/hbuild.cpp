@@ -287,12 +287,94 @@ void recompress(const std::vector<double>& A, const std::vector<double>& B, int 
   }
 }
 
+// Adaptive cross approximation with partial pivoting (Bebendorf): A B^T of the block of R with rows
+// r0..r1-1 and columns c0..c1-1 from single accurate entries, no kernel expansion.  Step k takes the
+// residual row at the pivot row i, its largest entry's column j, and the residual column j (scaled
+// by the pivot), and stops when |u_k| |v_k| <= eps |sum_l u_l v_l^T|_F (the norm updated
+// incrementally); the next pivot row is the largest unused entry of u_k.
+void aca_factors(const std::vector<double>& t, double alpha, int r0, int r1, int c0, int c1, double eps, int kmax,
+                 std::vector<double>& A, std::vector<double>& B, int& k) {
+  const int nr = r1 - r0, nc = c1 - c0;
+  std::vector<std::vector<double>> us, vs;
+  std::vector<char> row_used(nr, 0), col_used(nc, 0);
+  auto entry = [&](int r, int c) { return l1_entry(t, alpha, r0 + r + 1, c0 + c + 1); };
+  double norm2 = 0.0;
+  int i = 0;
+  for (int step = 0; step < kmax; ++step) {
+    std::vector<double> v(nc);
+    for (int c = 0; c < nc; ++c) {
+      double x = entry(i, c);
+      for (size_t l = 0; l < us.size(); ++l) x -= us[l][i] * vs[l][c];
+      v[c] = x;
+    }
+    row_used[i] = 1;
+    int j = -1;
+    double vmax = 0.0;
+    for (int c = 0; c < nc; ++c)
+      if (!col_used[c] && std::fabs(v[c]) > vmax) {
+        vmax = std::fabs(v[c]);
+        j = c;
+      }
+    if (j < 0 || vmax == 0.0) {  // this residual row vanishes: try the next unused row
+      int next = -1;
+      for (int r = 0; r < nr && next < 0; ++r)
+        if (!row_used[r]) next = r;
+      if (next < 0) break;
+      i = next;
+      continue;
+    }
+    col_used[j] = 1;
+    const double piv = v[j];
+    for (double& x : v) x /= piv;
+    std::vector<double> u(nr);
+    for (int r = 0; r < nr; ++r) {
+      double x = entry(r, j);
+      for (size_t l = 0; l < us.size(); ++l) x -= vs[l][j] * us[l][r];
+      u[r] = x;
+    }
+    double uu = 0.0, vv = 0.0;
+    for (double x : u) uu += x * x;
+    for (double x : v) vv += x * x;
+    for (size_t l = 0; l < us.size(); ++l) {
+      double uul = 0.0, vvl = 0.0;
+      for (int r = 0; r < nr; ++r) uul += u[r] * us[l][r];
+      for (int c = 0; c < nc; ++c) vvl += v[c] * vs[l][c];
+      norm2 += 2.0 * uul * vvl;
+    }
+    norm2 += uu * vv;
+    us.push_back(u);
+    vs.push_back(v);
+    if (std::sqrt(uu * vv) <= eps * std::sqrt(std::max(norm2, 0.0))) break;
+    int inext = -1;
+    double umax = -1.0;
+    for (int r = 0; r < nr; ++r)
+      if (!row_used[r] && std::fabs(u[r]) > umax) {
+        umax = std::fabs(u[r]);
+        inext = r;
+      }
+    if (inext < 0) break;
+    i = inext;
+  }
+  k = (int)us.size();
+  if (k == 0) {  // an all-zero block: one zero term
+    us.assign(1, std::vector<double>(nr, 0.0));
+    vs.assign(1, std::vector<double>(nc, 0.0));
+    k = 1;
+  }
+  A.assign((size_t)nr * k, 0.0);
+  B.assign((size_t)nc * k, 0.0);
+  for (int l = 0; l < k; ++l) {
+    for (int r = 0; r < nr; ++r) A[(size_t)r * k + l] = us[l][r];
+    for (int c = 0; c < nc; ++c) B[(size_t)c * k + l] = vs[l][c];
+  }
+}
+
 }  // namespace
 
 int build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,
-                  HostH& h) {
+                  HostH& h, int lowrank) {
   if (!(alpha > 0.0 && alpha < 1.0) || !(gamma >= 1.0) || !(T > 0.0) || M < 1 || leaf < 1 ||
-      rank < 0 || !(tol >= 0.0) || rank > 64)
+      rank < 0 || !(tol >= 0.0) || rank > 64 || (lowrank == 1 && !(rank == 0 && tol > 0.0)))
     return -1;
   int L = std::min(leaf, M);
   if (M % L) return -1;
@@ -347,6 +429,15 @@ int build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int ran
     rb.c0 = b[2];
     rb.c1 = b[3];
     std::vector<double> A, B;
+    if (lowrank == 1) {
+      int ka = 0;
+      aca_factors(h.t, alpha, b[0], b[1], b[2], b[3], 0.01 * tol, std::min(64, std::min(b[1] - b[0], b[3] - b[2])), A,
+                  B, ka);
+      recompress(A, B, b[1] - b[0], b[3] - b[2], ka, tol, rb);
+      h.max_rank = std::max(h.max_rank, rb.k);
+      h.rk.push_back(std::move(rb));
+      continue;
+    }
     taylor_factors(h.t, alpha, b[0], b[1], b[2], b[3], kt, A, B);
     if (rank > 0) {
       rb.k = kt;

@@ -137,10 +137,12 @@ void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out);
 // per-mode-group two-grid matrices with the time matrix replaced by its diagonal entries rdiag.
 double sama_two_grid(const std::vector<double>& rdiag, int dim, int N, double h, int nu1, int nu2);
 
-// Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).
+// Builds the H-matrix (or the dense lower-triangular R when rank == 0 && tol == 0).  lowrank 0:
+// admissible blocks from the Taylor expansion of the kernel (Section 3); 1 (needs rank == 0, tol > 0):
+// built algebraically from single entries by adaptive cross approximation, then recompressed.
 // Returns 0 on success, < 0 on invalid arguments.
 int build_hmatrix(double alpha, double gamma, double T, int M, int leaf, int rank, double tol,
-                  HostH& out);
+                  HostH& out, int lowrank = 0);
 void flatten(const HostH& h, FlatH& f);
 
 // Accurate single entry R_{m,j} (1-based, 1 <= j <= m), used for dense blocks.

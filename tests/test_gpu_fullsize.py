@@ -216,3 +216,23 @@ def test_recompressed_steps_against_dense_R(alpha, gamma, M, leaf):
     bnd = Ainv @ (_lowrank_row_bound(t, R, leaf, tol, Xd) + 4e-15 * (np.abs(R) @ np.abs(Xd)) + 4e-15 * s * np.abs(Xd))
     diff = np.abs(Xs.cpu().numpy() - Xd)
     assert np.all(diff <= 1.5 * bnd + 1e-15 * np.abs(Xd).max()), float((diff / (bnd + 1e-300)).max())
+
+
+@pytest.mark.parametrize("prec,tol", [(fh.FP64, 1e-8), (fh.MIXED_FP32, 1e-7)])
+def test_aca_hmatrix_solve_against_oracle(prec, tol):
+    """The H-matrix with algebraically built (adaptive cross approximation) low-rank blocks in a
+    full solve: 1D N=1023, M=2048, alpha=0.3 (gamma 5.67), manufactured source, relres 1e-8,
+    against the per-mode oracle with the dense R."""
+    alpha, M, N = 0.3, 2048, 1023
+    gamma = (2 - alpha) / alpha
+    t, R = oracle_R(alpha, gamma, M)
+    a, s = inputs.manufactured(t[1:], N, 1, alpha)
+    w = direct.solve_o2_mode(R, lam1d(N, 1.0 / (N + 1))[0], a)
+    H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10, lowrank="aca")
+    P = fh.Problem(H, 1, N, 1.0, prec)
+    f = dev(a)[:, None] * dev(s)[None, :]
+    u = torch.zeros_like(f)
+    k, rr = P.solve(u, f, None, 1, 1, 1e-8, 60)
+    ref = dev(w)[:, None] * dev(s)[None, :]
+    err = float((u - ref).abs().max() / ref.abs().max())
+    assert rr <= 1e-8 and err < tol, (k, rr, err)

@@ -148,20 +148,21 @@ def c5_net():
     return net
 
 
-@pytest.mark.parametrize("arm", ["fp64", "mixed", "mixed_warm"])
+@pytest.mark.parametrize("arm", ["fp64", "mixed", "mixed_warm", "bf16_warm"])
 def test_warmstart_workload_full_size(arm, c5_net):
     """2D N=1023^2, M=512, gamma=2, alpha=0.55, GRF source (length scale 0.1), relres 1e-8 of
     max|F|: the solution at 4096 sampled grid points (every time level) against the per-mode
-    oracle -- FP64 1e-8, mixed and mixed+warm 1e-7."""
+    oracle -- FP64 1e-8, mixed (FP32 or BF16 products) and mixed+warm 1e-7."""
     alpha, gamma, M, N, seed = 0.55, 2.0, 512, 1023, 31
     H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
     t, _ = H.mesh()
     f = warmstart.source_field(2, seed, t[1:], N)
-    P = fh.Problem(H, 2, N, 1.0, fh.FP64 if arm == "fp64" else fh.MIXED_FP32)
+    prec = {"fp64": fh.FP64, "bf16_warm": fh.MIXED_BF16}.get(arm, fh.MIXED_FP32)
+    P = fh.Problem(H, 2, N, 1.0, prec)
     P.set_coarse_direct(31)
     P.set_rtol_reference(1)
     u = torch.zeros_like(f)
-    if arm == "mixed_warm":
+    if arm.endswith("_warm"):
         c5_net.predict(P, f, alpha, K=24, bf16=True, u0=u)
     k, rr = P.solve(u, f, None, 1, 1, 1e-8, 60)
     rng = np.random.default_rng(77)

@@ -188,6 +188,17 @@ int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, Dev
 
 int blocks_for(long long n) { return fhmg::grid_for(n, 32); }
 
+// Launch shapes of the grid-function kernels (kernels.cuh): points along x, rows along y, time
+// levels strided along z.
+dim3 coarse_grid(int dim, int Nf, int M) {
+  const int Nc = (Nf - 1) / 2;
+  return fhmg::plane_grid(Nc, dim == 1 ? 1 : Nc, M, fhmg::device_sms());
+}
+dim3 fine_grid(int dim, int N, int M) { return fhmg::plane_grid(N, dim == 1 ? 1 : N, M, fhmg::device_sms()); }
+dim3 colour_grid(int dim, int N, int M) {
+  return fhmg::plane_grid((N + 1) / 2, dim == 1 ? 1 : N, M, fhmg::device_sms());
+}
+
 int check_dims(fhmg_problem p) {
   if (!p) return fail(FHMG_EINVAL, "null problem");
   return FHMG_OK;
@@ -398,9 +409,9 @@ template <typename T>
 int restrict_defect(fhmg_problem p, int l, const T* u, const T* F, T* rc, int kind) {
   LevelData& lv = p->lev[l];
   LevelData& lc = p->lev[l - 1];
-  const long long n = lc.npts * p->M;
   T* xs = scratch_X<T>(p);
-  fhmg::restrict_pre_kernel<T><<<blocks_for(n), 256, 0, p->st>>>(p->dim, lv.N, lv.inv_h2, p->M, u, F, xs, rc);
+  fhmg::restrict_pre_kernel<T><<<coarse_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, lv.inv_h2, p->M, u, F,
+                                                                                  xs, rc);
   ++p->launches;
   CK(cudaGetLastError());
   return walk_matvec<T>(p, kind, lc.npts, xs, rc, rc, nullptr);
@@ -408,8 +419,7 @@ int restrict_defect(fhmg_problem p, int l, const T* u, const T* F, T* rc, int ki
 
 template <typename T>
 int prolong_add(fhmg_problem p, int l, const T* e, T* u) {
-  const long long n = p->lev[l].npts * p->M;
-  fhmg::prolong_add_kernel<T><<<blocks_for(n), 256, 0, p->st>>>(p->dim, p->lev[l].N, p->M, e, u);
+  fhmg::prolong_add_kernel<T><<<fine_grid(p->dim, p->lev[l].N, p->M), 256, 0, p->st>>>(p->dim, p->lev[l].N, p->M, e, u);
   ++p->launches;
   CK(cudaGetLastError());
   return FHMG_OK;
@@ -565,8 +575,8 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
   CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), p->st));
   if (colour0_only && lv.npts > 1) {
     const long long nc = fhmg::colour_count(p->dim, lv.N, 0);
-    fhmg::gather_defect_kernel<double><<<blocks_for(nc * p->M), 256, 0, p->st>>>(p->dim, lv.N, 0, lv.inv_h2, p->M, u, F,
-                                                                                  p->Xs, p->Rs);
+    fhmg::gather_defect_kernel<double><<<colour_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, 0, lv.inv_h2,
+                                                                                        p->M, u, F, p->Xs, p->Rs);
     ++p->launches;
     CK(cudaGetLastError());
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
@@ -574,8 +584,8 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
   } else {
     double* dst = R ? R : p->Rs;
-    fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
-                                                                                       u, F, nullptr, dst);
+    fhmg::gather_defect_kernel<double><<<fine_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2,
+                                                                                      p->M, u, F, nullptr, dst);
     ++p->launches;
     CK(cudaGetLastError());
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
@@ -594,7 +604,8 @@ int full_rhs(fhmg_problem p, const double* f, const double* g, const double** F)
   }
   const long long npts = p->lev[p->nlev - 1].npts;
   if (!p->Ff) TRY(dalloc(p->allocs, &p->Ff, (size_t)npts * p->M));
-  fhmg::add_initial_kernel<double><<<blocks_for(npts * p->M), 256, 0, p->st>>>(npts, p->M, f, p->dmm, g, p->Ff);
+  fhmg::add_initial_kernel<double><<<fhmg::plane_grid(npts, 1, p->M, fhmg::device_sms()), 256, 0, p->st>>>(
+      npts, p->M, f, p->dmm, g, p->Ff);
   ++p->launches;
   CK(cudaGetLastError());
   *F = p->Ff;
@@ -758,8 +769,8 @@ int batched_vcycle(cudaStream_t st, std::vector<BLev> cur, int nu1, int nu2, int
     LevelData& lv = b.p->lev[b.l];
     LevelData& lc = b.p->lev[b.l - 1];
     const long long n = lc.npts * b.p->M;
-    fhmg::restrict_pre_kernel<double><<<blocks_for(n), 256, 0, st>>>(b.p->dim, lv.N, lv.inv_h2, b.p->M, b.u, b.F, b.p->Xs,
-                                                                      lc.RC);
+    fhmg::restrict_pre_kernel<double><<<coarse_grid(b.p->dim, lv.N, b.p->M), 256, 0, st>>>(b.p->dim, lv.N, lv.inv_h2,
+                                                                                         b.p->M, b.u, b.F, b.p->Xs, lc.RC);
     CK(cudaGetLastError());
     ++*nl;
     jobs.push_back(matvec_job<double>(b.p, kind, lc.npts, b.p->Xs, lc.RC, lc.RC, nullptr));
@@ -770,8 +781,8 @@ int batched_vcycle(cudaStream_t st, std::vector<BLev> cur, int nu1, int nu2, int
   TRY(batched_vcycle(st, next, nu1, nu2, kind, nl));
   for (auto& b : rest) {
     LevelData& lc = b.p->lev[b.l - 1];
-    const long long n = b.p->lev[b.l].npts * b.p->M;
-    fhmg::prolong_add_kernel<double><<<blocks_for(n), 256, 0, st>>>(b.p->dim, b.p->lev[b.l].N, b.p->M, lc.E, b.u);
+    fhmg::prolong_add_kernel<double><<<fine_grid(b.p->dim, b.p->lev[b.l].N, b.p->M), 256, 0, st>>>(
+        b.p->dim, b.p->lev[b.l].N, b.p->M, lc.E, b.u);
     CK(cudaGetLastError());
     ++*nl;
   }
@@ -786,8 +797,8 @@ int batched_defects(cudaStream_t st, std::vector<BLev>& set, std::vector<double*
     fhmg_problem p = set[i].p;
     LevelData& lv = p->lev[p->nlev - 1];
     CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), st));
-    fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
-                                                                                    set[i].u, set[i].F, nullptr, R[i]);
+    fhmg::gather_defect_kernel<double><<<fine_grid(p->dim, lv.N, p->M), 256, 0, st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
+                                                                                   set[i].u, set[i].F, nullptr, R[i]);
     CK(cudaGetLastError());
     ++*nl;
     jobs.push_back(matvec_job<double>(p, K64, lv.npts, set[i].u, R[i], R[i], p->dnorm));
@@ -803,8 +814,8 @@ int batched_colour0_norms(cudaStream_t st, std::vector<BLev>& set, long long* nl
     LevelData& lv = p->lev[p->nlev - 1];
     const long long nc = fhmg::colour_count(p->dim, lv.N, 0);
     CK(cudaMemsetAsync(p->dnorm, 0, sizeof(unsigned long long), st));
-    fhmg::gather_defect_kernel<double><<<blocks_for(nc * p->M), 256, 0, st>>>(p->dim, lv.N, 0, lv.inv_h2, p->M, b.u, b.F,
-                                                                               p->Xs, p->Rs);
+    fhmg::gather_defect_kernel<double><<<colour_grid(p->dim, lv.N, p->M), 256, 0, st>>>(p->dim, lv.N, 0, lv.inv_h2, p->M,
+                                                                                     b.u, b.F, p->Xs, p->Rs);
     CK(cudaGetLastError());
     ++*nl;
     jobs.push_back(matvec_job<double>(p, K64, nc, p->Xs, p->Rs, nullptr, p->dnorm));
@@ -874,8 +885,8 @@ int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, 
   ENTER(p);
   LevelData& lv = p->lev[p->nlev - 1];
   CK(cudaMemsetAsync(norm_word, 0, sizeof(unsigned long long), p->st));
-  fhmg::gather_defect_kernel<double><<<blocks_for(lv.npts * p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
-                                                                                     u, F, nullptr, B);
+  fhmg::gather_defect_kernel<double><<<fine_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
+                                                                                    u, F, nullptr, B);
   ++p->launches;
   CK(cudaGetLastError());
   TRY(walk_matvec<double>(p, defect_kind(p), lv.npts, u, B, nullptr, norm_word));

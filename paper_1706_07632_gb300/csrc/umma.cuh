@@ -139,7 +139,7 @@ __device__ __forceinline__ void put8_packed(unsigned char* tile, int c, int k0, 
 // T = float grid functions; the jobs' Dinv are the level inverses (without diagonal) in the
 // build_panel_umma layout (BF16 bits), ddiag the diagonal applied in FP32.
 template <int MODE>
-__global__ void __maxnreg__(200) humma_kernel(const __grid_constant__ WalkBatch<float, uint16_t> B) {
+__global__ void __maxnreg__(168) humma_kernel(const __grid_constant__ WalkBatch<float, uint16_t> B) {
   constexpr int L = kUmmaL, NT = kUmmaCols;
   extern __shared__ __align__(16) unsigned char sm[];
   const UmmaSmem lay = umma_smem(B.pool, B.W, B.slot_bytes, B.ns);

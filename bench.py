@@ -56,9 +56,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: FFMA units x clock (a
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / 11 / 1e12  # 7.32
 HEAD = dict(dim=2, N=1023, M=512, alpha=0.55, gamma=2.0, seed=999, K=24, nc=31)
 METRIC = "space-time DOF*cycles/s (time-to-1e-8 solve): mixed+warm-start vs plain FP64"
-# DRAM bytes per column of one launch, from the ncu captures named beside each (same kernels and
-# tiles on the 2D 255^2 x 512 case, scaled by columns); None where no capture of the current kernel
-TRAFFIC_PER_COLUMN = {}
+# DRAM bytes per column of one launch at M time levels, from the ncu captures named beside each
+# (same kernels and tiles on the 2D 255^2 x 512 case, scaled by columns); traffic is reported as
+# null for another M, and the entries are dropped whenever the kernel they describe changes
+TRAFFIC_PER_COLUMN = {
+    "smooth": (512, 349.2e6 / 32513),   # profiles/humma_smooth_2d_255x512.md
+    "defect": (512, 757.2e6 / 65025),   # profiles/hdf_defect_2d_255x512.md
+}
+
+
+def traffic(kind, M, ncols):
+    e = TRAFFIC_PER_COLUMN.get(kind)
+    return e[1] * ncols if e and e[0] == M else None
 
 
 def parse():
@@ -573,12 +582,11 @@ def roofline_smoother(H, cnt, ms_total, ncols, M, hbm_peak, bf16_peak, peak_kind
     flops_launch = H.flops_per_column() * ncols
     t_hbm = bytes_launch / (hbm_peak * 1e9)
     t_tc = flops_launch / (bf16_peak * 1e12)
-    tr = TRAFFIC_PER_COLUMN.get("smooth")
     common = {"kernel": "humma_kernel<SMOOTH> (finest-grid half-sweep, FP32 storage, BF16 tcgen05.mma, TMEM accumulators)",
               "avg_launch_ms": t * 1e3, "launches_timed": cnt["smooth_launches"],
               "share_of_step": cnt["smooth_ms"] / ms_total if ms_total > 0 else None,
               "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
-              "traffic": tr * ncols if tr else None}
+              "traffic": traffic("smooth", M, ncols)}
     if t_hbm >= t_tc:
         ach = bytes_launch / t / 1e9
         return dict(common, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
@@ -588,19 +596,18 @@ def roofline_smoother(H, cnt, ms_total, ncols, M, hbm_peak, bf16_peak, peak_kind
                 peak_note=f"BF16 dense, {peak_kind}")
 
 
-def roofline_defect(H, cnt, ms_total, ncols):
+def roofline_defect(H, cnt, ms_total, ncols, M):
     """The outer FP64-accurate defect (double-float products on the FP32 pipe), timed live."""
     n = max(cnt["defect_launches"], 1)
     t = cnt["defect_ms"] / n / 1e3
     flops_launch = H.flops_per_column() * ncols
     ach = flops_launch / t / 1e12
-    tr = TRAFFIC_PER_COLUMN.get("defect")
     return {"kernel": "hdf_kernel<64,8,MATVEC> (finest-grid FP64-accurate defect, double-float)", "bound": "alu",
             "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / DF_PEAK_TFLOPS,
             "peak_note": "152 SMs x 128 FP32 lanes/clk x 2.07 GHz x 2 flop per 11-instruction double-float multiply-add",
             "avg_launch_ms": t * 1e3, "launches_timed": cnt["defect_launches"],
             "share_of_step": cnt["defect_ms"] / ms_total if ms_total > 0 else None,
-            "algorithmic_flops_per_launch": flops_launch, "traffic": tr * ncols if tr else None}
+            "algorithmic_flops_per_launch": flops_launch, "traffic": traffic("defect", M, ncols)}
 
 
 def main():
@@ -662,7 +669,7 @@ def main():
     if rank == 0 and HEAD["N"] != 1023:
         print(f"note: headline grid {HEAD['N']}^2 (profiling size), not the workload's 1023^2", file=sys.stderr)
     rl_s = roofline_smoother(hd["H"], hd["cnt"], hd["ms"], ncol_colour, HEAD["M"], hbm_peak, bf16_peak, peak_kind)
-    rl_d = roofline_defect(hd["H"], hd["cnt"], hd["ms"], HEAD["N"] ** 2)
+    rl_d = roofline_defect(hd["H"], hd["cnt"], hd["ms"], HEAD["N"] ** 2, HEAD["M"])
     rl_head, rl_second = (rl_s, rl_d) if (rl_s["share_of_step"] or 0) >= (rl_d["share_of_step"] or 0) else (rl_d, rl_s)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DOF*cycles/s", "n_gpus": ws, "steps": a.steps,

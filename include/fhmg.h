@@ -215,13 +215,24 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
  * a warm start with the zero initial guess fairly. */
 int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
 
-/* Arithmetic of the mixed path's FP64-accurate steps -- the outer defect products (the residual
- * that decides convergence) and the mode solves of the exactly solved coarse level
- * (fhmg_problem_set_coarse_direct): 1 (default) double-float -- pairs of floats with error-free
- * transformations on the FP32 pipe (entries and x split as a = hi + lo, |a - hi - lo| <= 2^-48 |a|;
- * each dot product accurate to a few 2^-48 of sum |a_k x_k|), which on GB300 outruns the 1/64-rate
- * FP64 pipe; 0 FP64 (DFMA).  The stencil part and r = F - ... are FP64 in both. */
+/* Arithmetic of the mixed path's FP64-accurate steps -- the outer defect (the residual that decides
+ * convergence) and the mode solves of the exactly solved coarse level
+ * (fhmg_problem_set_coarse_direct).  0: FP64 (DFMA) products.  1: double-float -- pairs of floats
+ * with error-free transformations on the FP32 pipe (entries and x split as a = hi + lo,
+ * |a - hi - lo| <= 2^-48 |a|; each dot product accurate to a few 2^-48 of sum |a_k x_k|), which on
+ * GB300 outruns the 1/64-rate FP64 pipe; the stencil part and r = F - ... in FP64.  2 (the default
+ * where available: mixed problems with M a multiple of 128 and M <= 512): the outer defect on the
+ * tcgen05 tensor cores by error-free digit splitting (Ozaki et al. 2012) -- R~ (dense) and u are split
+ * per time row / per grid point into 7 base-2^7 digits of 49 bits, the digit products are summed
+ * exactly in FP32 tensor memory per digit-sum group, the groups are combined in double-float and
+ * the stencil in 64-bit fixed point; the error of (R~ u)_{m,c} is below
+ * (m+1) 2^{E_m + F_c - 46} + 2^-46 |(R~ u)_{m,c}| (2^E_m > max_k |R~_mk|, 2^F_c > max_k |u_kc|).
+ * The mode solves use double-float in modes 1 and 2.  EINVAL for mode 2 where it is not available. */
 int fhmg_problem_set_defect_arith(fhmg_problem p, int mode);
+/* BF16 tensor-core flops that one defect of defect arithmetic 2 executes per grid point (the
+ * digit-tile products of the split factors, all-zero R~ digit tiles left out); EINVAL where the
+ * problem has no such defect. */
+int fhmg_problem_split_flops(fhmg_problem p, double* per_point);
 
 /* FP32 products of the mixed path on the tensor cores (enable != 0, the default): with leaf 64,
  * walks with column tiles of 16 or 32 run as mma.sync m16n8k8 TF32 products split in three

@@ -68,6 +68,7 @@ _SIGS = {
     "fhmg_problem_set_coarse_direct": (_I, [_P, _I]),
     "fhmg_problem_set_tensor_cores": (_I, [_P, _I]),
     "fhmg_problem_set_defect_arith": (_I, [_P, _I]),
+    "fhmg_problem_split_flops": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
     "fhmg_problem_set_cycle_index": (_I, [_P, _I]),
     "fhmg_problem_inject_timeout": (_I, [_P, _LL]),
     "fhmg_hmatvec_df": (_I, [_P, _P, _P, _LL, _I]),
@@ -224,8 +225,16 @@ class Problem:
         _check(lib().fhmg_problem_inject_timeout(self._p, consumer_spin))
 
     def set_defect_arith(self, mode):
-        """Outer defect products of the mixed path: 1 double-float (default), 0 FP64."""
+        """Outer defect of the mixed path: 2 digit splitting on the tensor cores (the default where
+        available), 1 double-float walk, 0 FP64 products."""
         _check(lib().fhmg_problem_set_defect_arith(self._p, mode))
+
+    def split_flops(self):
+        """BF16 tensor-core flops per grid point of one split defect (None where unavailable)."""
+        v = ctypes.c_double()
+        if lib().fhmg_problem_split_flops(self._p, ctypes.byref(v)) != FHMG_OK:
+            return None
+        return v.value
 
     def hmatvec_df(self, Y, X, tile=0):
         _check(lib().fhmg_hmatvec_df(self._p, _ptr(Y), _ptr(X), X.numel() // self.M, tile))

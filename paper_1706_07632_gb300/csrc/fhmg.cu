@@ -90,7 +90,15 @@ struct fhmg_problem_s {
   DevPanel panel32m; // the same in the tensor-core layout (build_panel_mma)
   DevPanel panel64df; // FP64-accurate products in double-float arithmetic (build_panel_df)
   DevPanel panel32u;  // BF16 products on tcgen05 for the FP32-storage walks (build_panel_umma; BF16 problems)
-  int defect_df = 1;  // mixed path: the outer FP64 defect's products in double-float arithmetic
+  int defect_df = 1;  // mixed path, outer FP64 defect: 0 DFMA products, 1 double-float walk, 2 digit
+                      // splitting on the tensor cores (where split_ok)
+  // tensor-core defect by digit splitting (build_split): digit tiles of the dense R~, pair table,
+  // row exponents, per-point exponent scratch; mixed problems with M a multiple of 128, M <= 512
+  const unsigned char* spAt = nullptr;
+  const int* spPairs = nullptr;
+  const int* spRexp = nullptr;
+  int* spFe = nullptr;
+  double sp_mma_flops = 0;  // BF16 tensor-core flops one split defect executes per grid point
   int use_mma = 1;   // FP32 products on the tensor cores where the column tile allows
   double* rdiag = nullptr;  // FP64 diagonal of R~'s diagonal blocks (mixed path) ...
   float* rdiag32 = nullptr; // ... and its FP32 copy (FP32 inner cycles)
@@ -187,6 +195,22 @@ int upload_panel(const fhmg::HostH& h, const fhmg::FlatH& f, int elem_bytes, Dev
 }
 
 int blocks_for(long long n) { return fhmg::grid_for(n, 32); }
+
+// R~ as a dense row-major M x M matrix (near-field blocks as stored, low-rank blocks expanded)
+void dense_of(const fhmg::HostH& h, std::vector<double>& R) {
+  const int M = h.M, L = h.L;
+  R.assign((size_t)M * M, 0.0);
+  for (auto& d : h.dense)
+    for (int r = 0; r < L; ++r)
+      for (int c = 0; c < L; ++c) R[(size_t)(d.bi * L + r) * M + d.bj * L + c] = d.D[(size_t)r * L + c];
+  for (auto& b : h.rk)
+    for (int r = b.r0; r < b.r1; ++r)
+      for (int c = b.c0; c < b.c1; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < b.k; ++k) s += b.U[(size_t)(r - b.r0) * b.k + k] * b.V[(size_t)(c - b.c0) * b.k + k];
+        R[(size_t)r * M + c] = s;
+      }
+}
 
 // Launch shapes of the grid-function kernels (kernels.cuh): points along x, rows along y, time
 // levels strided along z.
@@ -567,6 +591,54 @@ int defect_kind(fhmg_problem p) {
   return (p->prec != FHMG_FP64 && p->defect_df && p->panel64df.d.pkg) ? KDF : K64;
 }
 
+// The full FP64-accurate defect on the finest grid into dst (all points), its max-norm folded into
+// *norm_word (zeroed by the caller): the tensor-core digit splitting where the problem has it
+// (defect arithmetic 2), else the stencil gather and the walk of defect_kind.
+int full_defect(fhmg_problem p, const double* u, const double* F, double* dst, unsigned long long* norm_word) {
+  LevelData& lv = p->lev[p->nlev - 1];
+  if (p->prec != FHMG_FP64 && p->defect_df == 2 && p->spAt) {
+    fhmg::SplitArgs a{};
+    a.U = u;
+    a.F = F;
+    a.OUT = dst;
+    a.norm = norm_word;
+    a.fe = p->spFe;
+    a.At = p->spAt;
+    a.pairs = reinterpret_cast<const int4*>(p->spPairs);
+    a.rexp = p->spRexp;
+    a.err = p->derr;
+    a.ld = lv.npts;
+    a.dim = p->dim;
+    a.N = lv.N;
+    a.M = p->M;
+    a.ih_hi = (float)lv.inv_h2;
+    a.ih_lo = (float)(lv.inv_h2 - (double)a.ih_hi);
+    if (p->inj_spin > 0) {
+      a.spin = p->inj_spin;
+      a.withhold = 2;
+      p->inj_spin = 0;
+    }
+    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
+    std::string err;
+    const int s = fhmg::split_defect_launch(p->st, a, &err);
+    p->launches += 2;
+    if (s == 1) return fail(FHMG_ECUDA, "%s", err.c_str());
+    if (s == 0) {
+      if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
+      return FHMG_OK;
+    }
+    return fail(FHMG_EINVAL, "%s", err.c_str());
+  }
+  fhmg::gather_defect_kernel<double><<<fine_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2,
+                                                                                    p->M, u, F, nullptr, dst);
+  ++p->launches;
+  CK(cudaGetLastError());
+  if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
+  TRY(walk_matvec<double>(p, defect_kind(p), lv.npts, u, dst, dst, norm_word));
+  if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
+  return FHMG_OK;
+}
+
 // FP64 defect on the finest grid.  colour0_only (after a completed red-black sweep the defect
 // vanishes on colour 1 up to rounding): max-norm over colour 0 only, nothing stored.
 // Otherwise the full defect is written to R (if R != NULL) and its max-norm returned.
@@ -583,14 +655,7 @@ int fine_defect(fhmg_problem p, const double* u, const double* F, bool colour0_o
     TRY(walk_matvec<double>(p, K64, nc, p->Xs, p->Rs, nullptr, p->dnorm));
     if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
   } else {
-    double* dst = R ? R : p->Rs;
-    fhmg::gather_defect_kernel<double><<<fine_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2,
-                                                                                      p->M, u, F, nullptr, dst);
-    ++p->launches;
-    CK(cudaGetLastError());
-    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
-    TRY(walk_matvec<double>(p, defect_kind(p), lv.npts, u, dst, R ? R : nullptr, p->dnorm));
-    if (p->profile) TRY(record_event(p, p->evd, p->evd_used));
+    TRY(full_defect(p, u, F, R ? R : p->Rs, p->dnorm));
   }
   return read_norm(p, out);
 }
@@ -885,11 +950,7 @@ int fhmg_internal_defect_norm(fhmg_problem p, const double* u, const double* F, 
   ENTER(p);
   LevelData& lv = p->lev[p->nlev - 1];
   CK(cudaMemsetAsync(norm_word, 0, sizeof(unsigned long long), p->st));
-  fhmg::gather_defect_kernel<double><<<fine_grid(p->dim, lv.N, p->M), 256, 0, p->st>>>(p->dim, lv.N, -1, lv.inv_h2, p->M,
-                                                                                    u, F, nullptr, B);
-  ++p->launches;
-  CK(cudaGetLastError());
-  TRY(walk_matvec<double>(p, defect_kind(p), lv.npts, u, B, nullptr, norm_word));
+  TRY(full_defect(p, u, F, B, norm_word));
   unsigned long long bits = 0;
   int derr = 0;
   CK(cudaMemcpyAsync(&bits, norm_word, sizeof bits, cudaMemcpyDeviceToHost, p->st));
@@ -977,18 +1038,9 @@ int fhmg_hmatrix_mesh(fhmg_hmatrix h, double* t_out, double* dmm_out) {
 
 int fhmg_hmatrix_dense(fhmg_hmatrix h, double* R) {
   if (!h || !R) return fail(FHMG_EINVAL, "null argument");
-  const int M = h->host.M, L = h->host.L;
-  std::memset(R, 0, sizeof(double) * M * M);
-  for (auto& d : h->host.dense)
-    for (int r = 0; r < L; ++r)
-      for (int c = 0; c < L; ++c) R[(size_t)(d.bi * L + r) * M + d.bj * L + c] = d.D[(size_t)r * L + c];
-  for (auto& b : h->host.rk)
-    for (int r = b.r0; r < b.r1; ++r)
-      for (int c = b.c0; c < b.c1; ++c) {
-        double s = 0.0;
-        for (int k = 0; k < b.k; ++k) s += b.U[(size_t)(r - b.r0) * b.k + k] * b.V[(size_t)(c - b.c0) * b.k + k];
-        R[(size_t)r * M + c] = s;
-      }
+  std::vector<double> D;
+  dense_of(h->host, D);
+  std::memcpy(R, D.data(), sizeof(double) * D.size());
   return FHMG_OK;
 }
 
@@ -1079,6 +1131,30 @@ int fhmg_problem_create(fhmg_hmatrix h, int dim, int N, double Lx, int prec, voi
     const float* d32;
     if ((st = upload(p->allocs, rd, &d32, nullptr)) != FHMG_OK) return bail(st);
     p->rdiag32 = const_cast<float*>(d32);
+    if (p->M % fhmg::kSplitRows == 0 && p->M <= fhmg::kSplitMaxM) {
+      std::vector<double> Rd;
+      dense_of(h->host, Rd);
+      fhmg::SplitHost sh;
+      fhmg::build_split(Rd, p->M, sh);
+      const unsigned char* at;
+      std::vector<unsigned char> bytes(sh.tiles.size() * 2);
+      std::memcpy(bytes.data(), sh.tiles.data(), bytes.size());
+      if ((st = upload(p->allocs, bytes, &at, nullptr)) != FHMG_OK) return bail(st);
+      p->spAt = at;
+      if ((st = upload(p->allocs, sh.pairs, &p->spPairs, nullptr)) != FHMG_OK) return bail(st);
+      if ((st = upload(p->allocs, sh.rexp, &p->spRexp, nullptr)) != FHMG_OK) return bail(st);
+      long long npts = 1;
+      for (int d = 0; d < dim; ++d) npts *= N;
+      if ((st = dalloc(p->allocs, &p->spFe, (size_t)npts)) != FHMG_OK) return bail(st);
+      // per 64-point tile: every stored digit tile a of a pair meets the u digits b < 7 - a in one
+      // 128 x 64 x 64 product each
+      double fl = 0;
+      for (size_t q = 0; q < sh.pairs.size(); q += 4)
+        for (int a = 0; a < 7; ++a)
+          if ((sh.pairs[q] >> a) & 1) fl += (7 - a) * 2.0 * 128 * 64 * 64;
+      p->sp_mma_flops = fl / 64;
+      p->defect_df = 2;
+    }
   }
   const int M = p->M;
   for (int l = 0; l < nlev; ++l) {
@@ -1302,9 +1378,19 @@ int fhmg_problem_set_coarse_direct(fhmg_problem p, int n) {
   return FHMG_OK;
 }
 
+int fhmg_problem_split_flops(fhmg_problem p, double* per_point) {
+  ENTER(p);
+  if (!per_point) return fail(FHMG_EINVAL, "null argument");
+  if (!p->spAt) return fail(FHMG_EINVAL, "no split defect for this problem");
+  *per_point = p->sp_mma_flops;
+  return FHMG_OK;
+}
+
 int fhmg_problem_set_defect_arith(fhmg_problem p, int mode) {
   ENTER(p);
-  if (mode != 0 && mode != 1) return fail(FHMG_EINVAL, "defect arithmetic must be 0 (FP64) or 1 (double-float)");
+  if (mode < 0 || mode > 2) return fail(FHMG_EINVAL, "defect arithmetic must be 0 (FP64), 1 (double-float) or 2 (splitting)");
+  if (mode == 2 && !p->spAt)
+    return fail(FHMG_EINVAL, "defect arithmetic 2 needs a mixed-precision problem with M a multiple of 128, M <= 512");
   p->defect_df = mode;
   return FHMG_OK;
 }

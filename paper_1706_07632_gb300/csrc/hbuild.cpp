@@ -910,6 +910,57 @@ void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out) {
     for (int k = 0; k < L; ++k) out[umma_offset(r, k, L) / 2] = bf16_bits((zero_diag && k == r) ? 0.0 : A[(size_t)r * L + k]);
 }
 
+void build_split(const std::vector<double>& R, int M, SplitHost& out) {
+  constexpr int G = 7, TR = 128, TK = 64;
+  const int nI = M / TR;
+  out.tiles.clear();
+  out.pairs.clear();
+  out.rexp.assign(M, 0);
+  // digits of every entry, row-major per digit
+  std::vector<int> dig((size_t)G * M * M, 0);
+  for (int m = 0; m < M; ++m) {
+    double mx = 0.0;
+    for (int k = 0; k <= m; ++k) mx = std::max(mx, std::fabs(R[(size_t)m * M + k]));
+    int E = 0;
+    if (mx > 0.0) std::frexp(mx, &E);
+    out.rexp[m] = E;
+    for (int k = 0; k <= m; ++k) {
+      long long X = std::llrint(std::ldexp(R[(size_t)m * M + k], 49 - E));
+      for (int a = G - 1; a >= 1; --a) {
+        const long long d = ((X + 64) & 127) - 64;
+        dig[((size_t)a * M + m) * M + k] = (int)d;
+        X = (X - d) / 128;
+      }
+      dig[(size_t)m * M + k] = (int)X;
+    }
+  }
+  const size_t tile_elems = (size_t)TR * TK;
+  for (int I = 0; I < nI; ++I)
+    for (int J = 0; J <= 2 * I + 1; ++J) {
+      int mask = 0;
+      const int first = (int)(out.tiles.size() / tile_elems);
+      for (int a = 0; a < G; ++a) {
+        bool any = false;
+        for (int r = 0; r < TR && !any; ++r)
+          for (int kk = 0; kk < TK; ++kk)
+            if (dig[((size_t)a * M + I * TR + r) * M + J * TK + kk] != 0) {
+              any = true;
+              break;
+            }
+        if (!any) continue;
+        mask |= 1 << a;
+        const size_t base = out.tiles.size();
+        out.tiles.resize(base + tile_elems, 0);
+        for (int r = 0; r < TR; ++r)
+          for (int kk = 0; kk < TK; ++kk) {
+            const int d = dig[((size_t)a * M + I * TR + r) * M + J * TK + kk];
+            out.tiles[base + umma_offset(r, kk, TK) / 2] = bf16_bits((double)d);
+          }
+      }
+      out.pairs.insert(out.pairs.end(), {mask, first, 0, 0});
+    }
+}
+
 void to_mma_layout(const double* A, int L, bool zero_diag, float* out) {
   const int nkb = (L + 15) / 16;
   std::vector<unsigned char> buf((size_t)nkb * 16 * nkb * 16 * 2 * 4, 0);

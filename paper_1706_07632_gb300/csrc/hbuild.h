@@ -133,6 +133,21 @@ size_t umma_offset(int r, int k, int K);
 // The row-major L x L matrix A in that layout (BF16 bits, L*L values), optionally without its diagonal.
 void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out);
 
+// Digit tiles of the tensor-core defect (split.cuh) from the dense time matrix R (row-major M x M,
+// lower triangular, M a multiple of 128).  Row m gets the exponent E_m = frexp exponent of
+// max_k |R_mk| (so max_k |R_mk| < 2^E_m; 0 for a zero row); R_mk 2^{49 - E_m} rounded to an
+// integer X is split into 7 balanced base-2^7 digits, X = sum_a d_a 2^{7 (6 - a)} (|d_0| <= 129,
+// the others in [-64, 64]), from the least significant up.  For every output block I (rows
+// 128 I ..) and K-block J <= 2 I + 1 (columns 64 J ..), I-major, the digit tiles a whose entries are
+// not all zero are stored in ascending a, each 128 x 64 BF16 in the umma_offset layout (K = 64);
+// pairs holds {mask of the stored digits, index of the first stored tile, 0, 0} per (I, J).
+struct SplitHost {
+  std::vector<uint16_t> tiles;
+  std::vector<int> pairs;
+  std::vector<int> rexp;
+};
+void build_split(const std::vector<double>& R, int M, SplitHost& out);
+
 // Two-grid convergence factor by mode analysis (sama.cpp): the largest spectral radius of the
 // per-mode-group two-grid matrices with the time matrix replaced by its diagonal entries rdiag.
 double sama_two_grid(const std::vector<double>& rdiag, int dim, int N, double h, int nu1, int nu2);

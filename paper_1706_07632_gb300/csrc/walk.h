@@ -49,6 +49,32 @@ int walk_launch_ff(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std
 int walk_launch_umma(cudaStream_t st, const WalkArgsT<float>* jobs, int njobs, std::string* err);
 constexpr int kUmmaL = 64;  // leaf size of the tcgen05 walk
 
+// FP64-accurate finest-grid defect r = F - A_h u - (R~ (x) I) u on the tcgen05 tensor cores by
+// digit splitting of R~ and u (split.cuh, walk_split.cu): time matrices with M a multiple of
+// kSplitRows and at most kSplitMaxM levels.  Launches the exponent pass and the defect kernel;
+// returns 2 for unsupported arguments.
+constexpr int kSplitRows = 128;
+constexpr int kSplitMaxM = 512;
+struct SplitArgs {
+  const double* U;            // u, [M][ld]
+  const double* F;            // F = f + d g, [M][ld]
+  double* OUT;                // r, [M][ld]
+  unsigned long long* norm;   // max |r| as FP64 bits (atomicMax), or NULL
+  int* fe;                    // scratch, ld ints: per grid point the largest biased FP64 exponent of u
+  const unsigned char* At;    // R~ digit tiles (build_split)
+  const int4* pairs;          // per (I, J), I-major: {digit mask, first tile, 0, 0}
+  const int* rexp;            // E_m per time row
+  int* err;                   // device error word (bounded-wait timeout)
+  long long ld;               // points per time level (N^dim)
+  long long ntiles;           // set by the launcher
+  int dim, N, M;
+  float ih_hi, ih_lo;         // 1 / h^2 as a float pair
+  int ns;                     // ring slots, set by the launcher
+  long long spin;             // consumer / MMA poll limit (0: kSpinLimit)
+  long long withhold;         // test hook (0 off): the producer withholds digit tile withhold - 1
+};
+int split_defect_launch(cudaStream_t st, const SplitArgs& a, std::string* err);
+
 int walk_launch_dfprod(cudaStream_t st, const WalkArgsT<double>* jobs, int njobs, std::string* err, int* tile_used);
 
 // Tensor-core walks (FP32 products, leaf 64, TC 16 or 32), walk_mma.cu.  B.ns is chosen here.

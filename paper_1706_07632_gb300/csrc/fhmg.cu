@@ -611,6 +611,7 @@ int full_defect(fhmg_problem p, const double* u, const double* F, double* dst, u
     a.dim = p->dim;
     a.N = lv.N;
     a.M = p->M;
+    a.inv_h2 = lv.inv_h2;
     a.ih_hi = (float)lv.inv_h2;
     a.ih_lo = (float)(lv.inv_h2 - (double)a.ih_hi);
     if (p->inj_spin > 0) {

@@ -954,7 +954,9 @@ void build_split(const std::vector<double>& R, int M, SplitHost& out) {
         for (int r = 0; r < TR; ++r)
           for (int kk = 0; kk < TK; ++kk) {
             const int d = dig[((size_t)a * M + I * TR + r) * M + J * TK + kk];
-            out.tiles[base + umma_offset(r, kk, TK) / 2] = bf16_bits((double)d);
+            // K-major, 128-byte swizzle: 16-byte chunk c of row r at chunk position c ^ (r % 8)
+            const size_t off = (size_t)(r / 8) * 1024 + (r % 8) * 128 + (size_t)(((kk / 8) ^ (r % 8)) & 7) * 16 + (kk % 8) * 2;
+            out.tiles[base + off / 2] = bf16_bits((double)d);
           }
       }
       out.pairs.insert(out.pairs.end(), {mask, first, 0, 0});

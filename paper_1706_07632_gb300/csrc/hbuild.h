@@ -139,7 +139,8 @@ void to_umma_layout(const double* A, int L, bool zero_diag, uint16_t* out);
 // integer X is split into 7 balanced base-2^7 digits, X = sum_a d_a 2^{7 (6 - a)} (|d_0| <= 129,
 // the others in [-64, 64]), from the least significant up.  For every output block I (rows
 // 128 I ..) and K-block J <= 2 I + 1 (columns 64 J ..), I-major, the digit tiles a whose entries are
-// not all zero are stored in ascending a, each 128 x 64 BF16 in the umma_offset layout (K = 64);
+// not all zero are stored in ascending a, each 128 x 64 BF16, K-major with the 128-byte swizzle
+// (row r's 16-byte chunk c at (r / 8) 1024 + (r % 8) 128 + (c ^ (r % 8)) 16);
 // pairs holds {mask of the stored digits, index of the first stored tile, 0, 0} per (I, J).
 struct SplitHost {
   std::vector<uint16_t> tiles;

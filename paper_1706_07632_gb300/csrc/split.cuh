@@ -25,7 +25,7 @@
 // Kernel.  A CTA owns tiles of 64 grid points (MMA N = 64) and walks the output blocks I of 128
 // time rows (MMA M = 128; TMEM lane = time row).  For every K-block J <= 2I+1 of 64 time levels
 // the consumer warps split u's block J of the tile into the G digit tiles (B operands, 64 x 64,
-// K-major, double-buffered), one MMA thread multiplies them with the streamed digit tiles of R~'s
+// K-major, 128-byte swizzle, double-buffered), one MMA thread multiplies them with the digit tiles of R~'s
 // block (I, J) (A operands, 128 x 64, produced by build_split, all-zero digit tiles left out) into
 // the G group accumulators (G x 64 TMEM columns), and after the last J the consumer warps read the
 // groups back (tcgen05.ld) and form r.  A producer warp streams the R~ digit tiles through an
@@ -71,6 +71,21 @@ __host__ __device__ inline SplitSmem split_smem(int ns) {
   return s;
 }
 
+// ---- operand layout: K-major, 128-byte swizzle ----
+// A tile row holds its 64 K entries (BF16) in 128 bytes; 8-row groups form 1024-byte atoms in which
+// the 16-byte chunk c of row r sits at chunk position c ^ (r % 8) (the tensor core reads the atoms
+// without bank conflicts).  Tiles start on 1024-byte boundaries.
+__host__ __device__ inline uint32_t sp_sw128_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ r) & 7) << 4) + (k & 7) * 2);
+}
+// shared-memory descriptor of such a tile: start address, leading byte offset unused (1), 8-row
+// groups 1024 bytes apart, fixed bits 46-48 = 0b001, swizzle mode 128B (2 in bits 61-63); a K step
+// of 16 entries (32 bytes) advances the start address field by 2
+__device__ __forceinline__ uint64_t sp_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)2 << 61);
+}
+
 // ---- integer views of FP64 values (no FP64 arithmetic) ----
 
 // round(|x| * 2^-s) for the 53-bit significand mt of x, s >= -7 (left shift) .. (>= 64: 0)
@@ -108,6 +123,50 @@ __device__ __forceinline__ double sp_f2d_scaled(float f, int k) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)ed << 52) | mant));
 }
 
+// FP64 nearest (up to one rounding of the smaller part) to (h + l) 2^k for a float pair, by integer
+// operations: the 24-bit significand of the part with the larger exponent is widened to 53 bits and
+// the other one's added at its offset (dropped below 2^-25 of its last place); zero: the other alone.
+__device__ __forceinline__ double sp_join(float h, float l, int k) {
+  uint32_t hb = __float_as_uint(h), lb = __float_as_uint(l);
+  if (((lb >> 23) & 0xFF) > ((hb >> 23) & 0xFF)) {  // the larger exponent leads (then d <= 29 below)
+    const uint32_t x = hb;
+    hb = lb;
+    lb = x;
+  }
+  const int eh = (int)((hb >> 23) & 0xFF), el = (int)((lb >> 23) & 0xFF);
+  if (eh == 0) return sp_f2d_scaled(l, k);
+  long long Mh = (long long)((hb & 0x7FFFFF) | 0x800000) << 29;  // units 2^{eh - 127 - 52}
+  if (hb >> 31) Mh = -Mh;
+  if (el != 0) {
+    const int d = el - eh + 29;  // l's significand in units of Mh's last place: shift by d
+    const long long ml = (long long)((lb & 0x7FFFFF) | 0x800000);
+    long long Ml = d >= 0 ? (ml << d) : (d > -25 ? ((ml + (1LL << (-d - 1))) >> (-d)) : 0);
+    if (lb >> 31) Ml = -Ml;
+    Mh += Ml;
+  }
+  if (Mh == 0) return 0.0;
+  const unsigned long long sign = Mh < 0 ? (1ULL << 63) : 0ULL;
+  unsigned long long a = (unsigned long long)(Mh < 0 ? -Mh : Mh);
+  int e = eh - 127 - 52 + k;  // value = a 2^e
+  const int lz = __clzll((long long)a);  // normalise to 53 bits (bit 52 set)
+  if (lz > 11) {
+    a <<= (lz - 11);
+    e -= lz - 11;
+  } else if (lz < 11) {
+    const int sh = 11 - lz;
+    a = (a + (1ULL << (sh - 1))) >> sh;
+    e += sh;
+    if (a >> 53) {
+      a >>= 1;
+      ++e;
+    }
+  }
+  const long long ed = (long long)e + 52 + 1023;
+  if (ed <= 0) return 0.0;
+  if (ed >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ULL));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)ed << 52) | (a & 0xFFFFFFFFFFFFFULL)));
+}
+
 // (h, l) = a + b exactly
 __device__ __forceinline__ void sp_two_sum(float a, float b, float& h, float& l) {
   h = __fadd_rn(a, b);
@@ -115,10 +174,39 @@ __device__ __forceinline__ void sp_two_sum(float a, float b, float& h, float& l)
   l = __fadd_rn(__fsub_rn(a, __fsub_rn(h, bb)), __fsub_rn(b, bb));
 }
 
+// float nearest to the integer a, |a| < 2^63, and the exact remainder a - that float; integer
+// operations only (the 64-bit conversion instructions run on the FP64 pipe)
+__device__ __forceinline__ float sp_ll2f(long long a, long long& rem) {
+  if (a == 0) {
+    rem = 0;
+    return 0.f;
+  }
+  const uint32_t sign = a < 0 ? 0x80000000u : 0u;
+  const unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
+  const int msb = 63 - __clzll((long long)m);
+  unsigned long long q;
+  int e = msb;
+  if (msb <= 23) {
+    q = m << (23 - msb);  // exact
+  } else {
+    const int sh = msb - 23;
+    q = (m + (1ULL << (sh - 1))) >> sh;  // round half up
+    if (q >> 24) {
+      q >>= 1;
+      ++e;
+    }
+  }
+  const uint32_t bits = sign | ((uint32_t)(e + 127) << 23) | (uint32_t)(q & 0x7FFFFF);
+  const long long back = msb <= 23 ? (long long)m : (long long)(q << (e - 23));
+  rem = a < 0 ? back - (long long)m : (long long)m - back;
+  return __uint_as_float(bits);
+}
+
 // int64 D -> float pair (hi = fl(D), lo = fl(D - hi)): relative error 2^-48
 __device__ __forceinline__ void sp_ll2df(long long D, float& h, float& l) {
-  h = __ll2float_rn(D);
-  l = __ll2float_rn(D - __float2ll_rn(h));
+  long long r, r2;
+  h = sp_ll2f(D, r);
+  l = sp_ll2f(r, r2);
 }
 
 // two digits as a BF16 pair (the first in the low half)
@@ -150,33 +238,119 @@ __device__ __forceinline__ void sp_digits(long long X, int (&d)[kSpG]) {
   d[0] = hi;
 }
 
-// per grid point: the largest biased exponent of u over the M time levels
-__global__ void split_colexp_kernel(const double* __restrict__ U, long long ld, int M, int* __restrict__ fe) {
+// FP64 value (bits) -> float pair (hi = RN(x) to 24 bits, lo = x - hi to 24 bits; relative error
+// 2^-48) scaled by 2^-s, by integer operations (the conversion instructions run on the FP64 pipe);
+// the pair must stay in the float normal range after the scaling (values below it become 0)
+__device__ __forceinline__ void sp_d2df(unsigned long long b, int s, float& h, float& l) {
+  const int e = (int)((b >> 52) & 0x7FF);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int fe = e - 1023 + 127 - s;  // float exponent field of x 2^-s
+  if (e == 0 || fe <= 24) {
+    h = l = 0.f;
+    return;
+  }
+  const unsigned long long mt = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  unsigned long long q = (mt + (1ULL << 28)) >> 29;  // 24-bit significand, round half up
+  int feh = fe;
+  if (q >> 24) {
+    q >>= 1;
+    ++feh;
+  }
+  h = __uint_as_float(sign | ((uint32_t)feh << 23) | (uint32_t)(q & 0x7FFFFF));
+  // remainder mt - q 2^{29 (+1)}: |r| <= 2^28 (exact in 32 bits), value r 2^{e - 1075 - s}
+  const long long back = (long long)(q << (29 + (feh - fe)));
+  const int r = (int)((long long)mt - back);
+  const float rf = __int2float_rn(r);  // 29 bits rounded to 24: relative 2^-48 of x
+  const int k = fe - 127 - 52;         // 2^{e - 1075 - s}
+  l = (sign ? -rf : rf) * sp_pow2f(k);
+}
+
+// (h, l) += (bh, bl), renormalised so that |l| <= ulp(h) / 2
+__device__ __forceinline__ void sp_df_add(float& h, float& l, float bh, float bl) {
+  float s2, e;
+  sp_two_sum(h, bh, s2, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s2, e);
+  l = __fsub_rn(e, __fsub_rn(h, s2));
+}
+
+// Pre-pass, one thread per grid point (grid-stride), over the M time levels: fe[p] = the largest
+// biased exponent of u at p, and B = F - A_h u written to B -- the defect kernel then subtracts R~ u
+// in place.  The stencil runs in double-float arithmetic on values scaled by 2^{-q}, q the exponent
+// of the largest of the five values at that time level, as sum_i (u_c - u_i) over the 2 dim
+// neighbours (missing ones 0): every difference exact in its high part, the running sum renormalised
+// after each term, so the error stays a few 2^-48 of |A_h| |u|; joined to FP64 with integer
+// operations, then one FP64 subtraction.  Two time levels in three take the plain FP64 route instead
+// (four FMA / subtractions and one FMA, a few 2^-53 of |A_h| |u|): the FP64 pipe and the integer /
+// FP32 pipes then share the work.  An Inf or NaN in the stencil gives NaN.
+__global__ void __launch_bounds__(256) split_prep_kernel(const double* __restrict__ U, const double* __restrict__ F,
+                                                         double* __restrict__ B, int* __restrict__ fe, long long ld,
+                                                         int M, int dim, int N, double ih, float ih_hi,
+                                                         float ih_lo) {
+  const unsigned long long* u = reinterpret_cast<const unsigned long long*>(U);
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < ld; p += (long long)gridDim.x * blockDim.x) {
+    const int ix = dim == 2 ? (int)(p % N) : (int)p;
+    const int iy = dim == 2 ? (int)(p / N) : 0;
+    const long long o0 = ix > 0 ? p - 1 : p, o1 = ix < N - 1 ? p + 1 : p;
+    const long long o2 = (dim == 2 && iy > 0) ? p - N : p, o3 = (dim == 2 && iy < N - 1) ? p + N : p;
+    const unsigned long long k0 = ix > 0 ? ~0ULL : 0ULL, k1 = ix < N - 1 ? ~0ULL : 0ULL;
+    const unsigned long long k2 = (dim == 2 && iy > 0) ? ~0ULL : 0ULL, k3 = (dim == 2 && iy < N - 1) ? ~0ULL : 0ULL;
     unsigned int mx = 0;
-    const unsigned long long* u = reinterpret_cast<const unsigned long long*>(U) + p;
-    int m = 0;
-    for (; m + 8 <= M; m += 8) {
-      unsigned long long v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = __ldg(u + (long long)(m + j) * ld);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) mx = max(mx, (unsigned int)((v[j] >> 52) & 0x7FF));
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+      const long long r = (long long)m * ld;
+      const unsigned long long bc = __ldg(u + r + p);
+      const unsigned long long x0 = __ldg(u + r + o0) & k0, x1 = __ldg(u + r + o1) & k1;
+      const unsigned long long x2 = __ldg(u + r + o2) & k2, x3 = __ldg(u + r + o3) & k3;
+      const double f = __ldg(F + r + p);
+      auto ex = [](unsigned long long b) { return (int)((b >> 52) & 0x7FF); };
+      const int ec = ex(bc);
+      mx = max(mx, (unsigned int)ec);
+      if (m % 3 != 2) {
+        auto d = [](unsigned long long b) { return __longlong_as_double((long long)b); };
+        double t = fma(dim == 2 ? 4.0 : 2.0, d(bc), -d(x0));
+        t = (t - d(x1)) - (d(x2) + d(x3));
+        B[r + p] = fma(-ih, t, f);
+        continue;
+      }
+      const int ql = max(max(ec, ex(x0)), max(max(ex(x1), ex(x2)), ex(x3)));
+      const int sc = ql - 1023 - 3;  // values scaled below 2^4
+      float ch, cl, h = 0.f, l = 0.f;
+      sp_d2df(bc, sc, ch, cl);
+      auto term = [&](unsigned long long x) {  // (h, l) += u_c - x
+        float nh, nl, s2, e;
+        sp_d2df(x, sc, nh, nl);
+        sp_two_sum(ch, -nh, s2, e);
+        sp_df_add(h, l, s2, __fadd_rn(e, __fsub_rn(cl, nl)));
+      };
+      term(x0);
+      term(x1);
+      if (dim == 2) {
+        term(x2);
+        term(x3);
+      }
+      // times 1/h^2 (float pair), then renormalised
+      const float sh = __fmul_rn(h, ih_hi);
+      float sl = __fmaf_rn(h, ih_hi, -sh);
+      sl = __fmaf_rn(h, ih_lo, __fmaf_rn(l, ih_hi, sl));
+      float th, tl;
+      sp_two_sum(sh, sl, th, tl);
+      B[r + p] = ql == 2047 ? __longlong_as_double(0x7FF8000000000000LL) : f - sp_join(th, tl, sc);
     }
-    for (; m < M; ++m) mx = max(mx, (unsigned int)((__ldg(u + (long long)m * ld) >> 52) & 0x7FF));
     fe[p] = (int)mx;
   }
 }
 
 struct SpCol {
-  int fe;     // the point's exponent (biased)
-  int qb;     // max of fe over the point and its neighbours (2047: an Inf or NaN among them)
-  int nbr;    // neighbour flags: 1 x-1, 2 x+1, 4 y-1, 8 y+1
+  int fe;     // the point's exponent (biased; 2047: an Inf or NaN in u at the point, r := NaN)
   int valid;
+  int pad0, pad1;
 };
 
 __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_constant__ SplitArgs A) {
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  // the swizzled operand tiles need 1024-byte aligned addresses (the launcher adds 1 KB)
+  unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
   const SplitSmem lay = split_smem(A.ns);
   const int ns = A.ns;
   unsigned char* ring = sm + lay.ring;
@@ -295,6 +469,11 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
             tc_after_sync();
             const int4 pd = __ldg(A.pairs + I * (I + 1) + J);
             const uint32_t xb = smem_u32(xbuf + (size_t)b * kSpG * kSpBtile);
+            // operand descriptors (K-major, 128-byte swizzle); a K step of 16 adds 2
+            uint64_t bdesc[kSpG];
+#pragma unroll
+            for (int bb = 0; bb < kSpG; ++bb) bdesc[bb] = sp_desc_sw128(xb + (uint32_t)bb * kSpBtile);
+            const uint32_t idesc = umma_idesc(kSpCols);
             for (int a = 0; a < kSpG; ++a) {
               if (!((pd.x >> a) & 1)) continue;
               if (!mbar_wait_or_abort(full + slot, (uint32_t)((k / ns) & 1), abort_flag, A.spin)) {
@@ -302,10 +481,20 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
                 break;
               }
               tc_after_sync();
-              const uint32_t aa = smem_u32(ring + (size_t)slot * kSpAtile);
-              for (int bb = 0; bb + a < kSpG; ++bb) {
+              const uint64_t adesc = sp_desc_sw128(smem_u32(ring + (size_t)slot * kSpAtile));
+#pragma unroll
+              for (int bb = 0; bb < kSpG; ++bb) {
+                if (bb + a >= kSpG) break;
                 const int gg = a + bb;
-                umma_product(tmem + 64u * gg, aa, xb + (uint32_t)bb * kSpBtile, kSpK, kSpCols, (touched >> gg) & 1);
+                const uint32_t d = tmem + 64u * gg;
+                const uint32_t acc0 = (touched >> gg) & 1;
+#pragma unroll
+                for (int st = 0; st < kSpK / 16; ++st)
+                  asm volatile(
+                      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                      "l"(adesc + 2ULL * st), "l"(bdesc[bb] + 2ULL * st), "r"(idesc), "r"(st > 0 ? 1u : acc0)
+                      : "memory");
                 touched |= 1 << gg;
               }
               umma_commit(empty + slot);
@@ -344,7 +533,6 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
     cbphase ^= 1;
     return !give_up(ok);
   };
-  const int N = A.N;
   const long long ld = A.ld;
   const unsigned long long* Ub = reinterpret_cast<const unsigned long long*>(A.U);
   // split: thread t owns point n = t & 63 of the tile and 16 time levels (t >> 6) * 16 .. of a K-block
@@ -355,31 +543,17 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
   unsigned long long nmax = 0;
   long long q = 0, nblk = 0;
   const int npairs = nI * (nI + 1);
-  auto ex = [](unsigned long long b) { return (int)((b >> 52) & 0x7FF); };
 
-  // L2 prefetch of the rows that block I's epilogue reads (this thread's time row, its 32 points,
-  // their neighbours and F): issued when the block's first pair is split, so that the HBM and
-  // address-translation latency of these row-strided reads overlaps the block's MMAs
+  // L2 prefetch of the B rows that block I's epilogue reads (this thread's time row, its 32 points):
+  // issued when the block's first pair is split, so that their latency overlaps the block's MMAs
   auto prefetch_block = [&](long long p0, int I) {
     const int m = I * kSpRows + wq * 32 + lane;
     const long long pc = p0 + ch * 32;
-    const unsigned long long* urow = Ub + (long long)m * ld;
-    const double* frow = A.F + (long long)m * ld;
-    auto pf = [&](const void* row, long long i) {
-      i = i < 0 ? 0 : (i >= ld ? ld - 1 : i);
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const double*>(row) + i));
-    };
+    const double* orow = A.OUT + (long long)m * ld;
 #pragma unroll
     for (int o = 0; o < 32; o += 16) {
-      pf(urow, pc + o - 1);
-      pf(urow, pc + o + 16);
-      pf(frow, pc + o);
-      if (A.dim == 2) {
-        pf(urow, pc + o - N);
-        pf(urow, pc + o + 15 - N);
-        pf(urow, pc + o + N);
-        pf(urow, pc + o + 15 + N);
-      }
+      const long long i = pc + o < ld ? pc + o : ld - 1;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(orow + i));
     }
   };
 
@@ -430,74 +604,29 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
         if (lane == 0) mbar_arrive(accfree);  // this warp is done with block I's accumulators
       }
       if (!consumer_meet()) return false;  // the half's piece is complete
-      // thread: point n = lane of the half, time rows w * 16 .. w * 16 + 15 of the block; the x
-      // neighbours come from the adjacent lanes (the half's edge lanes load theirs)
+      // thread: point n = lane of the half, time rows w * 16 .. w * 16 + 15 of the block:
+      // r = B - (R~ u), B = F - A_h u from the pre-pass (in OUT)
       const int n = lane;
       const SpCol c = col[half * 32 + n];
       const long long p = p0 + half * 32 + n;
       const long long pa = c.valid ? p : 0;
-      const long long pd0 = (c.nbr & 4) ? pa - N : pa, pu0 = (c.nbr & 8) ? pa + N : pa;
-      const long long pe = n == 0 ? ((c.nbr & 1) ? pa - 1 : pa) : ((c.nbr & 2) ? pa + 1 : pa);
-      const bool edge = n == 0 || n == 31;
-#pragma unroll 1
-      for (int r8 = 0; r8 < 16; r8 += 8) {
-        unsigned long long bc[8], bd[8], bu[8], be[8], fv[8];
+      double bv[16];
+      const double* bsrc = A.OUT + (long long)(I * kSpRows + w * 16) * ld + pa;
 #pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-          const long long row = (long long)(I * kSpRows + w * 16 + r8 + rr) * ld;
-          bc[rr] = __ldg(Ub + row + pa);
-          fv[rr] = __ldg(reinterpret_cast<const unsigned long long*>(A.F) + row + pa);
-          if (A.dim == 2) {
-            bd[rr] = __ldg(Ub + row + pd0);
-            bu[rr] = __ldg(Ub + row + pu0);
-          } else {
-            bd[rr] = bu[rr] = 0ULL;
-          }
-          be[rr] = edge ? __ldg(Ub + row + pe) : 0ULL;
-        }
+      for (int rr = 0; rr < 16; ++rr) bv[rr] = __ldcg(bsrc + (long long)rr * ld);
 #pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-          const int ml = w * 16 + r8 + rr;
-          const int m = I * kSpRows + ml;
-          const int Em = __ldg(A.rexp + m);
-          const float2 P = piece[(size_t)n * kSpPieceLd + ml];
-          const unsigned long long lft = __shfl_up_sync(0xffffffffu, bc[rr], 1);
-          const unsigned long long rgt = __shfl_down_sync(0xffffffffu, bc[rr], 1);
-          // stencil in 59-bit fixed point relative to the largest of its five values at this time
-          // level (biased exponent ql): X = round(u 2^{59 - (ql - 1022)}) = round(mt 2^{e - ql + 6})
-          const unsigned long long x0 = (c.nbr & 1) ? (n == 0 ? be[rr] : lft) : 0ULL;
-          const unsigned long long x1 = (c.nbr & 2) ? (n == 31 ? be[rr] : rgt) : 0ULL;
-          const unsigned long long x2 = (c.nbr & 4) ? bd[rr] : 0ULL, x3 = (c.nbr & 8) ? bu[rr] : 0ULL;
-          const int ql = max(max(ex(bc[rr]), ex(x0)), max(max(ex(x1), ex(x2)), ex(x3)));
-          const int sb = ql - 6;
-          const long long D = (A.dim == 2 ? 4 : 2) * sp_fixed(bc[rr], sb) - sp_fixed(x0, sb) - sp_fixed(x1, sb) -
-                              sp_fixed(x2, sb) - sp_fixed(x3, sb);
-          float dh, dl;
-          sp_ll2df(D, dh, dl);
-          // output scale 2^{Z - 1022}: the larger of the stencil's and of the bound 2^{E_m + F_c + 10}
-          // on |(R~ u)_{m,c}|; S' = D 2^{ql - Z - 59} / h^2 and y' = P 2^{E_m + fe - Z - 14} in its units
-          const int Z = max(ql, Em + c.fe + 10);
-          const float s59 = 1.7347234759768071e-18f;  // 2^-59
-          const float zs = sp_pow2f(ql - Z);
-          dh = (dh * s59) * zs;
-          dl = (dl * s59) * zs;
-          const float sh = __fmul_rn(dh, A.ih_hi);
-          float sl = __fmaf_rn(dh, A.ih_hi, -sh);
-          sl = __fmaf_rn(dh, A.ih_lo, __fmaf_rn(dl, A.ih_hi, sl));
-          const float ys = sp_pow2f(Em + c.fe - Z - 14);
-          const float yh = P.x * ys, yl = P.y * ys;
-          float th, tl;
-          sp_two_sum(sh, yh, th, tl);
-          tl = __fadd_rn(tl, __fadd_rn(sl, yl));
-          const int k = Z - 1022;
-          const double tsum = sp_f2d_scaled(th, k) + sp_f2d_scaled(tl, k);
-          const double r = c.qb == 2047 ? __longlong_as_double(0x7FF8000000000000LL)
-                                        : __longlong_as_double((long long)fv[rr]) - tsum;
-          if (c.valid) {
-            A.OUT[(long long)m * ld + p] = r;
-            const unsigned long long ab = (unsigned long long)__double_as_longlong(r) & 0x7FFFFFFFFFFFFFFFULL;
-            nmax = ab > nmax ? ab : nmax;
-          }
+      for (int rr = 0; rr < 16; ++rr) {
+        const int ml = w * 16 + rr;
+        const int m = I * kSpRows + ml;
+        const int Em = __ldg(A.rexp + m);
+        const float2 P = piece[(size_t)n * kSpPieceLd + ml];
+        // (R~ u)_{m,c} = 2^{E_m + F_c - 14} P, F_c = fe - 1022
+        const double y = sp_join(P.x, P.y, Em + c.fe - 1036);
+        const double r = c.fe == 2047 ? __longlong_as_double(0x7FF8000000000000LL) : bv[rr] - y;
+        if (c.valid) {
+          A.OUT[(long long)m * ld + p] = r;
+          const unsigned long long ab = (unsigned long long)__double_as_longlong(r) & 0x7FFFFFFFFFFFFFFFULL;
+          nmax = ab > nmax ? ab : nmax;
         }
       }
       if (!consumer_meet()) return false;  // every thread is done with the piece
@@ -517,14 +646,6 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
       if (p < ld) {
         c.valid = 1;
         c.fe = __ldg(A.fe + p);
-        const int ix = A.dim == 2 ? (int)(p % N) : (int)p;
-        const int iy = A.dim == 2 ? (int)(p / N) : 0;
-        int qb = c.fe;
-        if (ix > 0) { c.nbr |= 1; qb = max(qb, __ldg(A.fe + p - 1)); }
-        if (ix < N - 1) { c.nbr |= 2; qb = max(qb, __ldg(A.fe + p + 1)); }
-        if (A.dim == 2 && iy > 0) { c.nbr |= 4; qb = max(qb, __ldg(A.fe + p - N)); }
-        if (A.dim == 2 && iy < N - 1) { c.nbr |= 8; qb = max(qb, __ldg(A.fe + p + N)); }
-        c.qb = qb;  // 2047: an Inf or NaN in the stencil's points (r := NaN)
       }
       col[t] = c;
     }
@@ -576,7 +697,9 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
           for (int a = 0; a < kSpG; ++a) pk[a][j / 2] = sp_bf16pair(d0[a], d1[a]);
         }
 #pragma unroll
-        for (int a = 0; a < kSpG; ++a) put8_packed(xb + (size_t)a * kSpBtile, sn, sk + 8 * h, kSpK, pk[a]);
+        for (int a = 0; a < kSpG; ++a)
+          *reinterpret_cast<uint4*>(xb + (size_t)a * kSpBtile + sp_sw128_off(sn, sk + 8 * h)) =
+              make_uint4(pk[a][0], pk[a][1], pk[a][2], pk[a][3]);
       }
       async_proxy_fence();
       __syncwarp();

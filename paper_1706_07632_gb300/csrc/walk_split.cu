@@ -21,15 +21,16 @@ int split_defect_launch(cudaStream_t st, const SplitArgs& a0, std::string* err) 
   a.ntiles = (a.ld + kSpCols - 1) / kSpCols;
   if (a.spin <= 0) a.spin = kSpinLimit;
   const int sms = device_sms();
-  // the exponents of u per grid point (one pass over u, grid-stride)
-  split_colexp_kernel<<<grid_for(a.ld, 8), 256, 0, st>>>(a.U, a.ld, a.M, a.fe);
+  // the exponents of u per grid point and B = F - A_h u into OUT (one pass, grid-stride)
+  split_prep_kernel<<<grid_for(a.ld, 8), 256, 0, st>>>(a.U, a.F, a.OUT, a.fe, a.ld, a.M, a.dim, a.N, a.inv_h2,
+                                                       a.ih_hi, a.ih_lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    if (err) *err = std::string("split_colexp_kernel: ") + cudaGetErrorString(e);
+    if (err) *err = std::string("split_prep_kernel: ") + cudaGetErrorString(e);
     return 1;
   }
   a.ns = 4;
-  const size_t smem = split_smem(a.ns).total;
+  const size_t smem = split_smem(a.ns).total + 1024;  // + the alignment of the swizzled tiles
   int occ = 1;
   e = prepare_launch(split_defect_kernel, kSpBlock, smem, g_split_cache, &occ);
   if (e != cudaSuccess) {

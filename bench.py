@@ -61,7 +61,8 @@ METRIC = "space-time DOF*cycles/s (time-to-1e-8 solve): mixed+warm-start vs plai
 # (same kernels and tiles on the 2D 255^2 x 512 case, scaled by columns); traffic is reported as
 # null for another M, and the entries are dropped whenever the kernel they describe changes
 TRAFFIC_PER_COLUMN = {
-    "smooth": (512, 349.2e6 / 32513),   # profiles/humma_smooth_2d_255x512.md
+    "smooth": (512, 349.2e6 / 32513),                     # profiles/humma_smooth_2d_255x512.md
+    "defect": (512, (771.6e6 + 772.6e6) / 65025),         # profiles/split_defect_2d_255x512.md (both kernels)
 }
 
 
@@ -185,7 +186,7 @@ def head_config(rtol, tuned=True):
             "coarse_solve": f"exact solve of the {h['nc']}^2 level (DST-I in space, one H-matrix walk per mode)",
             "tiles": "autotuned (fhmg_problem_autotune)" if tuned else "heuristic",
             "warm_start": f"spectral MLP 6->320->320->320->1 (SiLU), BF16 inference, K={h['K']} modes per dimension",
-            "l2": "inputs larger than L2 (u, f 4.3 GB each)"}
+            "l2": f"inputs larger than L2 (u, f {h['N'] ** 2 * h['M'] * 8 / 1e9:.2f} GB each)"}
 
 
 # ------------------------------------------------------------------ oracle (timing + error checks)
@@ -614,8 +615,8 @@ def roofline_defect(H, cnt, ms_total, ncols, M, split_flops, bf16_peak, peak_kin
     if split_flops:
         mma = split_flops * ncols
         ach = mma / t / 1e12
-        return dict(common, kernel="split_defect_kernel (finest-grid FP64-accurate defect by BF16 digit splitting "
-                    "on tcgen05, exact FP32 group sums in TMEM)", bound="tensor", achieved=ach, peak=bf16_peak,
+        return dict(common, kernel="split_prep_kernel + split_defect_kernel (finest-grid FP64-accurate defect by "
+                    "BF16 digit splitting on tcgen05, exact FP32 group sums in TMEM)", bound="tensor", achieved=ach, peak=bf16_peak,
                     unit="TFLOP/s", frac=ach / bf16_peak, peak_note=f"BF16 dense sustained, {peak_kind}",
                     algorithmic_flops_per_launch=mma)
     ach = flops_launch / t / 1e12
@@ -693,7 +694,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
                 "config": head_config(a.rtol, not a.no_autotune),
                 "headline": ("mixed precision + learned warm start: network prediction of u0, then defect correction "
-                             "with double-float FP64-accurate outer defects around V-cycles with FP32 storage and "
+                             "with FP64-accurate outer defects (BF16 digit splitting on the tcgen05 tensor cores) around "
+                             "V-cycles with FP32 storage and "
                              "BF16 H-matrix products on the tcgen05 tensor cores (FP32 accumulation in tensor memory)"),
                 "cycle_unit": f"FP64 V(1,1) cycles to the target on the headline source = {k_ref}",
                 "arms": arms,

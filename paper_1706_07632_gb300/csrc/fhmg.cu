@@ -631,8 +631,6 @@ int full_defect(fhmg_problem p, const double* u, const double* F, double* dst, u
     a.N = lv.N;
     a.M = p->M;
     a.inv_h2 = lv.inv_h2;
-    a.ih_hi = (float)lv.inv_h2;
-    a.ih_lo = (float)(lv.inv_h2 - (double)a.ih_hi);
     if (p->inj_spin > 0) {
       a.spin = p->inj_spin;
       a.withhold = 2;

@@ -17,10 +17,9 @@
 // which costs at most a unit 2^-56 of the scale per accumulation step).  Then
 //     sum_k R~_mk u_kc = 2^{E_m + F_c - 14} sum_g 2^{-7g} A_g(m,c) + O((m+1) 2^{E_m + F_c - 46}),
 // the truncation coming from the 49-bit rounding of both factors and from the dropped groups
-// g >= 7.  The group sums are combined in double-float arithmetic; the stencil A_h u is formed in
-// 64-bit fixed point relative to the largest of its five values (59 bits); only the last two
-// subtractions run on the FP64 pipe (1/64 of the FP32 rate on GB300), so the FP64 values are split
-// and joined with integer operations.
+// g >= 7.  The group sums are combined in double-float arithmetic and joined to FP64 with integer
+// operations (the FP64 pipe runs at 1/64 of the FP32 rate on GB300); a pre-pass at full occupancy
+// forms B = F - A_h u in FP64 and the exponents F_c, and the kernel's epilogue writes r = B - R~ u.
 //
 // Kernel.  A CTA owns tiles of 64 grid points (MMA N = 64) and walks the output blocks I of 128
 // time rows (MMA M = 128; TMEM lane = time row).  For every K-block J <= 2I+1 of 64 time levels
@@ -174,40 +173,6 @@ __device__ __forceinline__ void sp_two_sum(float a, float b, float& h, float& l)
   l = __fadd_rn(__fsub_rn(a, __fsub_rn(h, bb)), __fsub_rn(b, bb));
 }
 
-// float nearest to the integer a, |a| < 2^63, and the exact remainder a - that float; integer
-// operations only (the 64-bit conversion instructions run on the FP64 pipe)
-__device__ __forceinline__ float sp_ll2f(long long a, long long& rem) {
-  if (a == 0) {
-    rem = 0;
-    return 0.f;
-  }
-  const uint32_t sign = a < 0 ? 0x80000000u : 0u;
-  const unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
-  const int msb = 63 - __clzll((long long)m);
-  unsigned long long q;
-  int e = msb;
-  if (msb <= 23) {
-    q = m << (23 - msb);  // exact
-  } else {
-    const int sh = msb - 23;
-    q = (m + (1ULL << (sh - 1))) >> sh;  // round half up
-    if (q >> 24) {
-      q >>= 1;
-      ++e;
-    }
-  }
-  const uint32_t bits = sign | ((uint32_t)(e + 127) << 23) | (uint32_t)(q & 0x7FFFFF);
-  const long long back = msb <= 23 ? (long long)m : (long long)(q << (e - 23));
-  rem = a < 0 ? back - (long long)m : (long long)m - back;
-  return __uint_as_float(bits);
-}
-
-// int64 D -> float pair (hi = fl(D), lo = fl(D - hi)): relative error 2^-48
-__device__ __forceinline__ void sp_ll2df(long long D, float& h, float& l) {
-  long long r, r2;
-  h = sp_ll2f(D, r);
-  l = sp_ll2f(r, r2);
-}
 
 // two digits as a BF16 pair (the first in the low half)
 __device__ __forceinline__ uint32_t sp_bf16pair(int d0, int d1) {
@@ -238,56 +203,15 @@ __device__ __forceinline__ void sp_digits(long long X, int (&d)[kSpG]) {
   d[0] = hi;
 }
 
-// FP64 value (bits) -> float pair (hi = RN(x) to 24 bits, lo = x - hi to 24 bits; relative error
-// 2^-48) scaled by 2^-s, by integer operations (the conversion instructions run on the FP64 pipe);
-// the pair must stay in the float normal range after the scaling (values below it become 0)
-__device__ __forceinline__ void sp_d2df(unsigned long long b, int s, float& h, float& l) {
-  const int e = (int)((b >> 52) & 0x7FF);
-  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-  const int fe = e - 1023 + 127 - s;  // float exponent field of x 2^-s
-  if (e == 0 || fe <= 24) {
-    h = l = 0.f;
-    return;
-  }
-  const unsigned long long mt = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-  unsigned long long q = (mt + (1ULL << 28)) >> 29;  // 24-bit significand, round half up
-  int feh = fe;
-  if (q >> 24) {
-    q >>= 1;
-    ++feh;
-  }
-  h = __uint_as_float(sign | ((uint32_t)feh << 23) | (uint32_t)(q & 0x7FFFFF));
-  // remainder mt - q 2^{29 (+1)}: |r| <= 2^28 (exact in 32 bits), value r 2^{e - 1075 - s}
-  const long long back = (long long)(q << (29 + (feh - fe)));
-  const int r = (int)((long long)mt - back);
-  const float rf = __int2float_rn(r);  // 29 bits rounded to 24: relative 2^-48 of x
-  const int k = fe - 127 - 52;         // 2^{e - 1075 - s}
-  l = (sign ? -rf : rf) * sp_pow2f(k);
-}
-
-// (h, l) += (bh, bl), renormalised so that |l| <= ulp(h) / 2
-__device__ __forceinline__ void sp_df_add(float& h, float& l, float bh, float bl) {
-  float s2, e;
-  sp_two_sum(h, bh, s2, e);
-  e = __fadd_rn(e, __fadd_rn(l, bl));
-  h = __fadd_rn(s2, e);
-  l = __fsub_rn(e, __fsub_rn(h, s2));
-}
-
 // Pre-pass, one thread per grid point (grid-stride), over the M time levels: fe[p] = the largest
-// biased exponent of u at p, and B = F - A_h u written to B -- the defect kernel then subtracts R~ u
-// in place.  The stencil runs in double-float arithmetic on values scaled by 2^{-q}, q the exponent
-// of the largest of the five values at that time level, as sum_i (u_c - u_i) over the 2 dim
-// neighbours (missing ones 0): every difference exact in its high part, the running sum renormalised
-// after each term, so the error stays a few 2^-48 of |A_h| |u|; joined to FP64 with integer
-// operations, then one FP64 subtraction.  Two time levels in three take the plain FP64 route instead
-// (four FMA / subtractions and one FMA, a few 2^-53 of |A_h| |u|): the FP64 pipe and the integer /
-// FP32 pipes then share the work.  An Inf or NaN in the stencil gives NaN.
+// biased exponent of u at p, and B = F - A_h u in FP64 (two FMAs and three subtractions: a few 2^-53
+// of |A_h| |u|, the accuracy the h^2 cancellation of fine grids needs) written to B -- the defect
+// kernel then subtracts R~ u in place.  An Inf or NaN in u or F propagates.
 __global__ void __launch_bounds__(256) split_prep_kernel(const double* __restrict__ U, const double* __restrict__ F,
                                                          double* __restrict__ B, int* __restrict__ fe, long long ld,
-                                                         int M, int dim, int N, double ih, float ih_hi,
-                                                         float ih_lo) {
+                                                         int M, int dim, int N, double ih) {
   const unsigned long long* u = reinterpret_cast<const unsigned long long*>(U);
+  const double cdiag = dim == 2 ? 4.0 : 2.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < ld; p += (long long)gridDim.x * blockDim.x) {
     const int ix = dim == 2 ? (int)(p % N) : (int)p;
     const int iy = dim == 2 ? (int)(p / N) : 0;
@@ -302,40 +226,11 @@ __global__ void __launch_bounds__(256) split_prep_kernel(const double* __restric
       const unsigned long long bc = __ldg(u + r + p);
       const unsigned long long x0 = __ldg(u + r + o0) & k0, x1 = __ldg(u + r + o1) & k1;
       const unsigned long long x2 = __ldg(u + r + o2) & k2, x3 = __ldg(u + r + o3) & k3;
-      const double f = __ldg(F + r + p);
-      auto ex = [](unsigned long long b) { return (int)((b >> 52) & 0x7FF); };
-      const int ec = ex(bc);
-      mx = max(mx, (unsigned int)ec);
-      if (m % 3 != 2) {
-        auto d = [](unsigned long long b) { return __longlong_as_double((long long)b); };
-        double t = fma(dim == 2 ? 4.0 : 2.0, d(bc), -d(x0));
-        t = (t - d(x1)) - (d(x2) + d(x3));
-        B[r + p] = fma(-ih, t, f);
-        continue;
-      }
-      const int ql = max(max(ec, ex(x0)), max(max(ex(x1), ex(x2)), ex(x3)));
-      const int sc = ql - 1023 - 3;  // values scaled below 2^4
-      float ch, cl, h = 0.f, l = 0.f;
-      sp_d2df(bc, sc, ch, cl);
-      auto term = [&](unsigned long long x) {  // (h, l) += u_c - x
-        float nh, nl, s2, e;
-        sp_d2df(x, sc, nh, nl);
-        sp_two_sum(ch, -nh, s2, e);
-        sp_df_add(h, l, s2, __fadd_rn(e, __fsub_rn(cl, nl)));
-      };
-      term(x0);
-      term(x1);
-      if (dim == 2) {
-        term(x2);
-        term(x3);
-      }
-      // times 1/h^2 (float pair), then renormalised
-      const float sh = __fmul_rn(h, ih_hi);
-      float sl = __fmaf_rn(h, ih_hi, -sh);
-      sl = __fmaf_rn(h, ih_lo, __fmaf_rn(l, ih_hi, sl));
-      float th, tl;
-      sp_two_sum(sh, sl, th, tl);
-      B[r + p] = ql == 2047 ? __longlong_as_double(0x7FF8000000000000LL) : f - sp_join(th, tl, sc);
+      mx = max(mx, (unsigned int)((bc >> 52) & 0x7FF));
+      auto d = [](unsigned long long b) { return __longlong_as_double((long long)b); };
+      double t = fma(cdiag, d(bc), -d(x0));
+      t = (t - d(x1)) - (d(x2) + d(x3));
+      B[r + p] = fma(-ih, t, __ldg(F + r + p));
     }
     fe[p] = (int)mx;
   }

@@ -69,7 +69,6 @@ struct SplitArgs {
   long long ntiles;           // set by the launcher
   int dim, N, M;
   double inv_h2;              // 1 / h^2
-  float ih_hi, ih_lo;         // ... and as a float pair
   int ns;                     // ring slots, set by the launcher
   long long spin;             // consumer / MMA poll limit (0: kSpinLimit)
   long long withhold;         // test hook (0 off): the producer withholds digit tile withhold - 1

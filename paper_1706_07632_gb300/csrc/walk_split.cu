@@ -22,8 +22,7 @@ int split_defect_launch(cudaStream_t st, const SplitArgs& a0, std::string* err) 
   if (a.spin <= 0) a.spin = kSpinLimit;
   const int sms = device_sms();
   // the exponents of u per grid point and B = F - A_h u into OUT (one pass, grid-stride)
-  split_prep_kernel<<<grid_for(a.ld, 8), 256, 0, st>>>(a.U, a.F, a.OUT, a.fe, a.ld, a.M, a.dim, a.N, a.inv_h2,
-                                                       a.ih_hi, a.ih_lo);
+  split_prep_kernel<<<grid_for(a.ld, 8), 256, 0, st>>>(a.U, a.F, a.OUT, a.fe, a.ld, a.M, a.dim, a.N, a.inv_h2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     if (err) *err = std::string("split_prep_kernel: ") + cudaGetErrorString(e);

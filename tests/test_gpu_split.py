@@ -6,9 +6,10 @@ Error bound (derived from the arithmetic): R~ and u are split per time row / per
 2^F_c > max_k |u_kc|.  Per term k the rounding of both factors costs <= 2^{E_m + F_c - 49} and the
 dropped digit groups (a + b >= 7) <= 2^{E_m + F_c - 48.4}; the group sums are exact integers in the
 FP32 accumulators except the last group, whose accumulation loses at most 2^{E_m + F_c - 48.2}
-per output; the double-float combination, the fixed-point stencil and the final FP64 subtractions
-add a few 2^-47 of |R~||u| + |A_h||u| + |F|.  With a factor 2 of margin:
-    |r - r_oracle| <= (m + 2) 2^{E_m + F_c - 46} + 2^-45 (|R~||u| + |A_h||u| + |F|).
+per output; the double-float combination of the groups adds a few 2^-47 of |R~||u|; the stencil and
+the subtractions run in FP64 (a few 2^-53 of |A_h||u| + |F| -- fine grids need it: at N = 4095 the
+stencil cancels 2^24-fold).  With a factor 2 of margin:
+    |r - r_oracle| <= (m + 2) 2^{E_m + F_c - 46} + 2^-45 |R~||u| + 2^-50 (|A_h||u| + |F|).
 The time matrix is the paper's rank-k Taylor form (or dense R), which the oracle builds itself.
 """
 import math
@@ -47,8 +48,9 @@ def split_bound(Rt, u, F, h):
     U = u.reshape(M, -1)
     Fc = np.array([math.frexp(float(x))[1] for x in np.abs(U).max(axis=0)], dtype=float)
     trunc = (np.arange(M) + 2.0)[:, None] * np.exp2(E[:, None] + Fc[None, :] - 46.0)
-    mag = np.abs(Rt) @ np.abs(U) + abs_stencil(u, h).reshape(M, -1) + np.abs(F).reshape(M, -1)
-    return (trunc + 2.0 ** -45 * mag).reshape(u.shape)
+    prod = np.abs(Rt) @ np.abs(U)
+    sten = abs_stencil(u, h).reshape(M, -1) + np.abs(F).reshape(M, -1)
+    return (trunc + 2.0 ** -45 * prod + 2.0 ** -50 * sten).reshape(u.shape)
 
 
 def time_matrix(alpha, gamma, M, leaf, rank):
@@ -81,6 +83,27 @@ def test_split_defect_against_oracle(dim, N, M, alpha, gamma, rank, prec):
     diff = np.abs(r.cpu().numpy() - ref)
     bound = split_bound(Rt, u, F, h)
     assert np.all(diff <= bound), float((diff / bound).max())
+
+
+@pytest.mark.parametrize("prec", [fh.MIXED_FP32, fh.MIXED_BF16])
+def test_split_solve_fine_1d_reaches_target(prec):
+    """1D N = 4095 (the stencil cancels 2^24-fold), M = 512: the mixed solve with the split defect
+    reaches relres 1e-8 and the per-mode oracle's solution to 1e-7 (a double-float stencil, 2^-48, would
+    leave the residual floor above 1e-8 here)."""
+    alpha, gamma, M, N = 0.8, 1.5, 512, 4095
+    t = l1.graded_mesh(1.0, M, gamma)
+    R = l1.l1_matrix(t, alpha)
+    H = fh.HMatrix(alpha, gamma, 1.0, M, 64, 0, 1e-10)
+    P = fh.Problem(H, 1, N, 1.0, prec)
+    assert P.split_flops() is not None
+    a, sx = inputs.manufactured(t[1:], N, 1, alpha)
+    w = direct.solve_o2_mode(R, direct.laplacian_eigs_1d(N, 1.0 / (N + 1))[0], a)
+    f = torch.as_tensor(np.outer(a, sx), device=DEV)
+    u = torch.zeros_like(f)
+    k, rr = P.solve(u, f, None, 1, 1, 1e-8, 60)
+    ref = np.outer(w, sx)
+    err = float(np.abs(u.cpu().numpy() - ref).max() / np.abs(ref).max())
+    assert rr <= 1e-8 and err < 1e-7, (k, rr, err)
 
 
 def test_split_matches_double_float_defect():

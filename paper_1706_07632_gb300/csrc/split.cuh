@@ -203,10 +203,36 @@ __device__ __forceinline__ void sp_digits(long long X, int (&d)[kSpG]) {
   d[0] = hi;
 }
 
+// FP64 value of the integer D times 2^k (D exact up to 53 bits, else rounded half up), by integer
+// operations; 0 below the FP64 normal range
+__device__ __forceinline__ double sp_ll2d(long long D, int k) {
+  if (D == 0) return 0.0;
+  const unsigned long long sign = D < 0 ? (1ULL << 63) : 0ULL;
+  unsigned long long a = (unsigned long long)(D < 0 ? -D : D);
+  int msb = 63 - __clzll((long long)a);
+  if (msb <= 52) {
+    a <<= (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    a = (a + (1ULL << (sh - 1))) >> sh;
+    if (a >> 53) {
+      a >>= 1;
+      ++msb;
+    }
+  }
+  const long long ed = (long long)msb + k + 1023;
+  if (ed <= 0) return 0.0;
+  if (ed >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ULL));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)ed << 52) | (a & 0xFFFFFFFFFFFFFULL)));
+}
+
 // Pre-pass, one thread per grid point (grid-stride), over the M time levels: fe[p] = the largest
-// biased exponent of u at p, and B = F - A_h u in FP64 (two FMAs and three subtractions: a few 2^-53
-// of |A_h| |u|, the accuracy the h^2 cancellation of fine grids needs) written to B -- the defect
-// kernel then subtracts R~ u in place.  An Inf or NaN in u or F propagates.
+// biased exponent of u at p, and B = F - A_h u written to B -- the defect kernel then subtracts R~ u
+// in place.  The stencil needs FP64 accuracy (at N = 4095 it cancels 2^24-fold).  Two time levels in
+// three form it with FP64 FMAs and subtractions (a few 2^-53 of |A_h| |u|); the third exactly in
+// 64-bit fixed point relative to the largest of its five values (59 bits), converted by integer
+// operations -- so the FP64 pipe (1/64 of the FP32 rate on GB300) and the integer pipe share the work
+// -- and both end with one FMA, B = F - S / h^2.  An Inf or NaN in u or F propagates.
 __global__ void __launch_bounds__(256) split_prep_kernel(const double* __restrict__ U, const double* __restrict__ F,
                                                          double* __restrict__ B, int* __restrict__ fe, long long ld,
                                                          int M, int dim, int N, double ih) {
@@ -220,17 +246,28 @@ __global__ void __launch_bounds__(256) split_prep_kernel(const double* __restric
     const unsigned long long k0 = ix > 0 ? ~0ULL : 0ULL, k1 = ix < N - 1 ? ~0ULL : 0ULL;
     const unsigned long long k2 = (dim == 2 && iy > 0) ? ~0ULL : 0ULL, k3 = (dim == 2 && iy < N - 1) ? ~0ULL : 0ULL;
     unsigned int mx = 0;
-#pragma unroll 4
+#pragma unroll 3
     for (int m = 0; m < M; ++m) {
       const long long r = (long long)m * ld;
       const unsigned long long bc = __ldg(u + r + p);
       const unsigned long long x0 = __ldg(u + r + o0) & k0, x1 = __ldg(u + r + o1) & k1;
       const unsigned long long x2 = __ldg(u + r + o2) & k2, x3 = __ldg(u + r + o3) & k3;
-      mx = max(mx, (unsigned int)((bc >> 52) & 0x7FF));
-      auto d = [](unsigned long long b) { return __longlong_as_double((long long)b); };
-      double t = fma(cdiag, d(bc), -d(x0));
-      t = (t - d(x1)) - (d(x2) + d(x3));
-      B[r + p] = fma(-ih, t, __ldg(F + r + p));
+      auto ex = [](unsigned long long b) { return (int)((b >> 52) & 0x7FF); };
+      mx = max(mx, (unsigned int)ex(bc));
+      double S;
+      if (m % 3 != 2) {
+        auto d = [](unsigned long long b) { return __longlong_as_double((long long)b); };
+        const double t = fma(cdiag, d(bc), -d(x0));
+        S = (t - d(x1)) - (d(x2) + d(x3));
+      } else {
+        // X = round(u 2^{59 - (ql - 1022)}) = round(mt 2^{e - ql + 6}); |D| < 2^62
+        const int ql = max(max(ex(bc), ex(x0)), max(max(ex(x1), ex(x2)), ex(x3)));
+        const int sb = ql - 6;
+        const long long D = (dim == 2 ? 4 : 2) * sp_fixed(bc, sb) - sp_fixed(x0, sb) - sp_fixed(x1, sb) -
+                            sp_fixed(x2, sb) - sp_fixed(x3, sb);
+        S = ql == 2047 ? __longlong_as_double(0x7FF8000000000000LL) : sp_ll2d(D, ql - 1022 - 59);
+      }
+      B[r + p] = fma(-ih, S, __ldg(F + r + p));
     }
     fe[p] = (int)mx;
   }

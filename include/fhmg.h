@@ -206,8 +206,9 @@ int fhmg_solve(fhmg_problem p, double* u, const double* f, const double* g, int 
  * Runs on an internal stream ordered after, and before, every problem's stream. */
 int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f, int nu1, int nu2,
                        double rtol, int max_cycles, int* cycles_out, double* relres_out);
-/* Autotuner for the leaf size: builds the H-matrix with leaf 32 and 64, autotunes the column
- * tiles of each, times one V-cycle, and returns the faster leaf (and its cycle time in ms). */
+/* Autotuner for the leaf size: builds the H-matrix with leaf 16, 32 and 64 (those <= M), autotunes
+ * the column tiles of each, times one V-cycle, and returns the fastest leaf (and its cycle time in
+ * ms).  (The tensor-core walks need leaf 64; smaller leaves trade them for fewer near-field entries.) */
 int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, int dim, int N, double Lx,
                        int prec, void* stream, int* best_leaf, double* best_ms);
 /* Stopping reference of fhmg_solve: 0 (default) ||r_k|| <= rtol ||r_0|| (the paper's test, §5);

@@ -1781,7 +1781,7 @@ int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, 
   if (!best_leaf) return fail(FHMG_EINVAL, "best_leaf is NULL");
   double best = 1e300;
   int bl = 0;
-  for (int leaf : {32, 64}) {
+  for (int leaf : {16, 32, 64}) {
     if (leaf > M) continue;
     fhmg_hmatrix h = nullptr;
     if (fhmg_build_hmatrix(alpha, gamma, T, M, leaf, 0, tol, &h) != FHMG_OK) continue;

@@ -113,7 +113,9 @@ int fhmg_problem_destroy(fhmg_problem p);
 /* Chooses the column tile of each kernel by timing (autotuner); optional. */
 int fhmg_problem_autotune(fhmg_problem p);
 /* Mixed path: V-cycles run on the correction equation between two FP64 defect evaluations
- * (>= 1; 0 restores the default: 2 with FP32 storage, 4 with FP64 storage). */
+ * (>= 1; 0 restores the default: 2 with FP32 storage, 4 with FP64 storage).  After the first round
+ * a round runs fewer cycles where the previous round's contraction per cycle predicts that fewer
+ * reach rtol with a factor 2 to spare (so the last round runs no cycle the target does not need). */
 int fhmg_problem_set_inner(fhmg_problem p, int inner_cycles);
 /* Mixed path, storage of the inner cycles: 0 automatic, per level: FP32 on every level whose
  * stencil conditioning allows it (6e-8 * 4 (N+1)^2 / pi^2 <= 0.05, i.e. N <= 1023), FP64 grid

@@ -790,23 +790,39 @@ int solve_mixed(fhmg_problem p, double* u, const double* F, int nu1, int nu2, do
   // it); FP64 storage with FP32 products converges like FP64 (four V-cycles ~ 1e-4)
   const int inner = p->inner > 0 ? p->inner : (f32 ? 2 : 4);
   int k = 0;
+  double r_prev = -1.0;
+  int last = 0;
   while (r > rtol * r0 && k < max_cycles) {
+    // cycles of this round: inner, or fewer where the previous round's contraction per cycle says
+    // that fewer reach the target with a factor 2 to spare (the last round then runs no cycle the
+    // target does not need; each round costs an FP64-accurate defect)
+    int cyc = inner;
+    if (r_prev > 0.0 && last > 0 && r < r_prev) {
+      const double rho = std::pow(r / r_prev, 1.0 / last);
+      if (rho > 0.0 && rho < 0.9) {
+        const double need = std::log(0.5 * rtol * r0 / r) / std::log(rho);
+        if (need < inner) cyc = std::max(1, (int)std::ceil(need));
+      }
+    }
+    const int k_round = k;
     if (f32) {
       to_float_kernel<<<blocks_for(n), 256, 0, p->st>>>(p->Rs, p->Rs32, n);
       ++p->launches;
       CK(cudaGetLastError());
       CK(cudaMemsetAsync(p->Ef32, 0, sizeof(float) * n, p->st));
-      for (int j = 0; j < inner && k < max_cycles; ++j, ++k)
+      for (int j = 0; j < cyc && k < max_cycles; ++j, ++k)
         TRY(vcycle_rec<float>(p, p->nlev - 1, p->Ef32, p->Rs32, nu1, nu2, K32));
       add_float_kernel<<<blocks_for(n), 256, 0, p->st>>>(u, p->Ef32, n);
       ++p->launches;
       CK(cudaGetLastError());
     } else {
       CK(cudaMemsetAsync(p->Ef, 0, sizeof(double) * n, p->st));
-      for (int j = 0; j < inner && k < max_cycles; ++j, ++k)
+      for (int j = 0; j < cyc && k < max_cycles; ++j, ++k)
         TRY(vcycle_rec<double>(p, p->nlev - 1, p->Ef, p->Rs, nu1, nu2, KSPLIT));
       TRY(axpy(p, u, p->Ef, n, 1.0));
     }
+    r_prev = r;
+    last = k - k_round;
     TRY(fine_defect(p, u, F, false, p->Rs, &r));
     if (!std::isfinite(r)) return fail(FHMG_ENAN, "residual became non-finite after %d cycles", k);
   }

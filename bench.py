@@ -62,7 +62,7 @@ METRIC = "space-time DOF*cycles/s (time-to-1e-8 solve): mixed+warm-start vs plai
 # null for another M, and the entries are dropped whenever the kernel they describe changes
 TRAFFIC_PER_COLUMN = {
     "smooth": (512, 349.2e6 / 32513),                     # profiles/humma_smooth_2d_255x512.md
-    "defect": (512, (771.4e6 + 772.8e6) / 65025),         # profiles/split_defect_2d_255x512.md (both kernels)
+    "defect": (512, (770.95e6 + 770.24e6) / 65025),       # profiles/split_defect_2d_255x512.md (both kernels)
 }
 
 

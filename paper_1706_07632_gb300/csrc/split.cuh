@@ -50,6 +50,7 @@ constexpr uint32_t kSpTmemCols = 512;
 constexpr int kSpAtile = kSpRows * kSpK * 2;    // bytes of one R~ digit tile
 constexpr int kSpBtile = kSpCols * kSpK * 2;    // bytes of one u digit tile
 constexpr int kSpPieceLd = kSpRows + 1;         // float pairs per point of the epilogue's piece (odd: no bank conflicts)
+static_assert((size_t)32 * kSpPieceLd * 8 <= (size_t)kSpG * kSpBtile, "a piece fits a digit buffer");
 
 struct SplitSmem {
   size_t ring, xbuf, stage, col, bar, total;
@@ -59,7 +60,8 @@ __host__ __device__ inline SplitSmem split_smem(int ns) {
   s.ring = 0;
   s.xbuf = (size_t)ns * kSpAtile;
   // the next K-block's u values ([64 levels][64 points] doubles); during an epilogue the same bytes hold
-  // the transposed block piece ([32 points][kSpPieceLd] float pairs)
+  // the transposed piece of points 0..31 ([32 points][kSpPieceLd] float pairs; points 32..63 go to
+  // the free digit buffer, kSpG * kSpBtile bytes)
   s.stage = s.xbuf + 2 * (size_t)kSpG * kSpBtile;
   const size_t stage_bytes = (size_t)kSpK * kSpCols * 8, piece_bytes = (size_t)32 * kSpPieceLd * 8;
   s.col = s.stage + (stage_bytes > piece_bytes ? stage_bytes : piece_bytes);
@@ -489,58 +491,65 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
     }
   };
 
-  // epilogue of output block I of the tile at p0 (its accumulators complete: accdone waited), in two
-  // halves of 32 points.  The four warps owning a half's TMEM columns fold the seven groups of their
-  // 32 time rows into double-float sums and write them transposed into the piece; those warps then
-  // release tensor memory (so the next block's MMAs start), and all eight warps form r thread per
-  // grid point, so that every global access is a contiguous row segment.
-  float2* piece = reinterpret_cast<float2*>(stage);
-  auto epilogue = [&](long long p0, int I) -> bool {
+  // epilogue of output block I of the tile at p0 (its accumulators complete: accdone waited).  Phase
+  // 1: all eight warps fold the seven groups of their 32 time rows x 32 points into double-float sums
+  // and write them transposed into the two pieces (points 0..31 in the staging bytes, points 32..63
+  // in digit buffer bfree, whose pair's MMAs completed with the block's), then release tensor memory,
+  // so that the next block's MMAs start while phase 2 runs.  Phase 2: thread per grid point, so that
+  // every global access is a contiguous row segment.
+  auto epilogue = [&](long long p0, int I, int bfree, auto&& mid) -> bool {
     const int mask = *gmask;
-    if (!consumer_meet()) return false;  // every warp has read its staged values (the piece reuses them)
-    for (int half = 0; half < 2; ++half) {
-      if (ch == half) {
-        const int ml = wq * 32 + lane;
+    float2* const piece0 = reinterpret_cast<float2*>(stage);
+    float2* const piece1 = reinterpret_cast<float2*>(xbuf + (size_t)bfree * kSpG * kSpBtile);
+    if (!consumer_meet()) return false;  // every warp has read its staged values (piece 0 reuses them)
+    {
+      float2* const pc = ch ? piece1 : piece0;
+      const int ml = wq * 32 + lane;
 #pragma unroll 1
-        for (int c8 = 0; c8 < 4; ++c8) {
-          const int n0 = half * 32 + c8 * 8;
-          float ph[8], pl[8];
+      for (int c8 = 0; c8 < 4; ++c8) {
+        const uint32_t n0 = (uint32_t)(ch * 32 + c8 * 8);
+        uint32_t r[kSpG][8];
 #pragma unroll
-          for (int gg = 0; gg < kSpG; ++gg) {
-            uint32_t r[8];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                : "r"(tmem + lane_base + 64u * gg + (uint32_t)n0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const bool live = (mask >> gg) & 1;
+        for (int gg = 0; gg < kSpG; ++gg)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+              : "=r"(r[gg][0]), "=r"(r[gg][1]), "=r"(r[gg][2]), "=r"(r[gg][3]), "=r"(r[gg][4]), "=r"(r[gg][5]),
+                "=r"(r[gg][6]), "=r"(r[gg][7])
+              : "r"(tmem + lane_base + 64u * gg + n0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // the loaded registers are read only after the wait
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float a = live ? __uint_as_float(r[j]) : 0.f;
-              if (gg == 0) {
-                ph[j] = a;
-                pl[j] = 0.f;
-              } else {
-                float s2, e;
-                sp_two_sum(ph[j], a * sp_pow2f(-7 * gg), s2, e);
-                ph[j] = s2;
-                pl[j] = __fadd_rn(pl[j], e);
-              }
-            }
+        for (int gg = 0; gg < kSpG; ++gg)
+          asm volatile("" : "+r"(r[gg][0]), "+r"(r[gg][1]), "+r"(r[gg][2]), "+r"(r[gg][3]), "+r"(r[gg][4]),
+                       "+r"(r[gg][5]), "+r"(r[gg][6]), "+r"(r[gg][7]));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float ph = (mask & 1) ? __uint_as_float(r[0][j]) : 0.f, pl = 0.f;
+#pragma unroll
+          for (int gg = 1; gg < kSpG; ++gg) {
+            const float a = ((mask >> gg) & 1) ? __uint_as_float(r[gg][j]) : 0.f;
+            float s2, e;
+            sp_two_sum(ph, a * sp_pow2f(-7 * gg), s2, e);
+            ph = s2;
+            pl = __fadd_rn(pl, e);
           }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) piece[(size_t)(c8 * 8 + j) * kSpPieceLd + ml] = make_float2(ph[j], pl[j]);
+          pc[(size_t)(c8 * 8 + j) * kSpPieceLd + ml] = make_float2(ph, pl);
         }
-        tc_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(accfree);  // this warp is done with block I's accumulators
       }
-      if (!consumer_meet()) return false;  // the half's piece is complete
-      // thread: point n = lane of the half, time rows w * 16 .. w * 16 + 15 of the block:
-      // r = B - (R~ u), B = F - A_h u from the pre-pass (in OUT)
-      const int n = lane;
-      const SpCol c = col[half * 32 + n];
-      const long long p = p0 + half * 32 + n;
+      tc_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accfree);  // this warp is done with block I's accumulators
+    }
+    if (!consumer_meet()) return false;  // the pieces are complete
+    // thread: point n = half * 32 + lane, time rows w * 16 .. + 15 of the block, half 0 first:
+    // r = B - (R~ u), B = F - A_h u from the pre-pass (in OUT).  Once every thread is done with piece
+    // 0, mid() may reuse the staging bytes (the next K-block's copies overlap half 1)
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      const int n = half * 32 + lane;
+      const float2* const pc = half ? piece1 : piece0;
+      const SpCol c = col[n];
+      const long long p = p0 + n;
       const long long pa = c.valid ? p : 0;
       double bv[16];
       const double* bsrc = A.OUT + (long long)(I * kSpRows + w * 16) * ld + pa;
@@ -551,7 +560,7 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
         const int ml = w * 16 + rr;
         const int m = I * kSpRows + ml;
         const int Em = __ldg(A.rexp + m);
-        const float2 P = piece[(size_t)n * kSpPieceLd + ml];
+        const float2 P = pc[(size_t)lane * kSpPieceLd + ml];
         // (R~ u)_{m,c} = 2^{E_m + F_c - 14} P, F_c = fe - 1022
         const double y = sp_join(P.x, P.y, Em + c.fe - 1036);
         const double r = c.fe == 2047 ? __longlong_as_double(0x7FF8000000000000LL) : bv[rr] - y;
@@ -561,9 +570,12 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
           nmax = ab > nmax ? ab : nmax;
         }
       }
-      if (!consumer_meet()) return false;  // every thread is done with the piece
+      if (half == 0) {
+        if (!consumer_meet()) return false;  // every thread is done with piece 0
+        mid();
+      }
     }
-    return true;
+    return consumer_meet();  // every thread is done with the pieces
   };
 
   for (long long g = blockIdx.x; g < A.ntiles && !failed; g += gridDim.x) {
@@ -640,22 +652,25 @@ __global__ void __launch_bounds__(kSpBlock, 1) split_defect_kernel(const __grid_
       const bool last = s + 1 == npairs;
       const bool epi = (J == 0 && I > 0) || last;
       // the next pair's copies only now (the proxy fence above waits for this thread's outstanding
-      // memory operations) and, when an epilogue runs here, after it (it uses the staging bytes)
+      // memory operations) and, when an epilogue runs here, once it is done with the staging bytes
       if (!epi && s + 1 < npairs) stage16(Jn);
       if (epi) {
         // epilogue of block I - 1 (or, at the tile's end, of the last block)
         const int Ie = last ? I : I - 1;
+        // the digit buffer of the pair split before this one: its MMAs completed with block Ie's
+        const int bfree = b ^ 1;
         if (give_up(mbar_wait_or_abort(accdone, (uint32_t)(nblk & 1), abort_flag, A.spin))) {
           failed = true;
           break;
         }
         tc_after_sync();
-        if (!epilogue(p0, Ie)) {
+        if (!epilogue(p0, Ie, bfree, [&]() {
+              if (s + 1 < npairs) stage16(Jn);
+            })) {
           failed = true;
           break;
         }
         ++nblk;
-        if (s + 1 < npairs) stage16(Jn);
       }
       I = In;
       J = Jn;

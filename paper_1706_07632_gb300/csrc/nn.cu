@@ -12,7 +12,8 @@
 // or BF16 inference.  Layer l maps width n_l to n_{l+1} with weights W_l (n_{l+1} x n_l,
 // row-major) and bias b_l; all parameters live in one FP32 array in layer order (W_0, b_0, W_1,
 // b_1, ...).  Kernels: tiled FP32 GEMM (64 x 64 tiles, 4 x 4 per thread, both transposes),
-// bias + SiLU forward / backward, MSE loss, column sums, Adam, feature build, spectral
+// BF16 tensor-core GEMMs for inference (hidden layers with bias and SiLU fused), bias + SiLU forward /
+// backward, MSE loss, column sums, Adam, feature build, spectral
 // projection and synthesis.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -138,6 +139,111 @@ __global__ void __launch_bounds__(128) gemm_bf16_nt(int M, int N, int K, const _
 }
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + __expf(-x)); }
+
+// BF16 inference layer with the bias and the activation fused: out = SiLU(A W^T + b), A (M x K) and
+// W (N x K) row-major BF16 (16-byte aligned rows), b FP32, K % 32 == 0, N % 64 == 0.  Block tile
+// 128 x 64; K tiles of 32 double-buffered in shared memory by cp.async (rows padded to 80 bytes:
+// the fragment loads below hit 32 distinct banks); 8 warps of 32 x 32, each a 2 x 4 grid of
+// mma.sync m16n8k16 tiles with FP32 accumulation, k16 steps in the same order as gemm_bf16_nt; the
+// epilogue adds b, applies SiLU and writes BF16 (the same FP32 operations as bias_act_fwd).
+__global__ void __launch_bounds__(256) gemm_bf16_silu(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                      const __nv_bfloat16* __restrict__ W,
+                                                      const float* __restrict__ bias, __nv_bfloat16* out) {
+  constexpr int BM = 128, BN = 64, BK = 32, LDS = BK + 8;
+  __shared__ __align__(16) __nv_bfloat16 sA[2][BM * LDS];
+  __shared__ __align__(16) __nv_bfloat16 sW[2][BN * LDS];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp & 3, wn = warp >> 2;
+  const int g = lane >> 2, q = lane & 3;
+  const long long m0 = (long long)blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  auto load_tile = [&](int buf, int k0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {  // A: 128 rows x 4 chunks of 16 bytes
+      const int c = tid + i * 256;
+      const int r = c >> 2, kc = (c & 3) * 8;
+      const long long gr = m0 + r;
+      const bool ok = gr < M;
+      const __nv_bfloat16* src = A + (ok ? gr : 0LL) * K + k0 + kc;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&sA[buf][r * LDS + kc])),
+                   "l"(src), "r"(ok ? 16 : 0)
+                   : "memory");
+    }
+    {  // W: 64 rows x 4 chunks
+      const int r = tid >> 2, kc = (tid & 3) * 8;
+      const __nv_bfloat16* src = W + (long long)(n0 + r) * K + k0 + kc;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&sW[buf][r * LDS + kc])),
+                   "l"(src)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto lds32 = [](const __nv_bfloat16* p) -> uint32_t { return *reinterpret_cast<const uint32_t*>(p); };
+  float acc[2][4][4];
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[mi][ni][j] = 0.f;
+  const int nk = K / BK;
+  load_tile(0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) {
+      load_tile((kt + 1) & 1, (kt + 1) * BK);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const __nv_bfloat16* a = sA[kt & 1];
+    const __nv_bfloat16* w = sW[kt & 1];
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bf[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int r = wm * 32 + mi * 16 + g;
+        af[mi][0] = lds32(a + r * LDS + ks + 2 * q);
+        af[mi][1] = lds32(a + (r + 8) * LDS + ks + 2 * q);
+        af[mi][2] = lds32(a + r * LDS + ks + 2 * q + 8);
+        af[mi][3] = lds32(a + (r + 8) * LDS + ks + 2 * q + 8);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int c = wn * 32 + ni * 8 + g;
+        bf[ni][0] = lds32(w + c * LDS + ks + 2 * q);
+        bf[ni][1] = lds32(w + c * LDS + ks + 2 * q + 8);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]), "r"(bf[ni][0]), "r"(bf[ni][1]));
+    }
+    __syncthreads();  // this buffer is refilled two tiles on
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int c = n0 + wn * 32 + ni * 8 + 2 * q;
+      const float b0 = bias[c], b1 = bias[c + 1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long r = m0 + wm * 32 + mi * 16 + g + 8 * h;
+        if (r >= M) continue;
+        const float z0 = acc[mi][ni][2 * h] + b0, z1 = acc[mi][ni][2 * h + 1] + b1;
+        *reinterpret_cast<__nv_bfloat162*>(out + r * N + c) = __floats2bfloat162_rn(z0 * sigm(z0), z1 * sigm(z1));
+      }
+    }
+}
 
 // Z += b (row broadcast); A = SiLU(Z) (act = 1) or Z (act = 0).  Z kept for the backward pass.
 __global__ void bias_act_fwd(int n, int w, float* Z, const float* b, float* A, int act, __nv_bfloat16* Abf) {
@@ -416,11 +522,23 @@ int fhmg_wsnet_forward(fhmg_wsnet net, const float* X, int n, int bf16, float* Y
   int cur = 0;
   for (int l = 0; l < L; ++l) {
     const int wi = net->width[l], wo = net->width[l + 1];
+    const bool last = l == L - 1;
+    const __nv_bfloat16* Wl = net->Pbf + net->woff[l];
+    if (!last && wi % 32 == 0 && wo % 64 == 0 && reinterpret_cast<uintptr_t>(Wl) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(net->Abf[cur]) % 16 == 0) {
+      // hidden layers of the full width: one tiled launch, bias and SiLU fused (Z is not needed:
+      // the backward pass runs on the FP32 forward's activations)
+      dim3 grid(wo / 64, (n + 127) / 128);
+      gemm_bf16_silu<<<grid, 256, 0, st>>>(n, wo, wi, net->Abf[cur], Wl, net->P + net->boff[l], net->Abf[1 - cur]);
+      ++g_nn_launches;
+      NCK(cudaGetLastError());
+      cur = 1 - cur;
+      continue;
+    }
     dim3 grid((wo + 7) / 8, (n + 63) / 64);
     gemm_bf16_nt<<<grid, 128, 0, st>>>(n, wo, wi, net->Abf[cur], net->Pbf + net->woff[l], net->Z[l]);
     ++g_nn_launches;
     NCK(cudaGetLastError());
-    const bool last = l == L - 1;
     bias_act_fwd<<<nblk((long long)n * wo), 256, 0, st>>>(n, wo, net->Z[l], net->P + net->boff[l],
                                                         last ? Y : nullptr, last ? 0 : 1,
                                                         last ? nullptr : net->Abf[1 - cur]);

@@ -1,5 +1,6 @@
-"""Warm-start network: gradients of the GPU kernels against the CPU oracle, BF16 inference, the
-training pairs against per-mode oracle solutions, and the cycles the trained network saves."""
+"""Warm-start network: gradients of the GPU kernels against the CPU oracle, BF16 inference (against
+FP32 and against a BF16 emulation), the training pairs against per-mode oracle solutions, and the
+cycles the trained network saves."""
 import math
 
 import numpy as np
@@ -42,6 +43,34 @@ def test_bf16_inference_close_to_fp32():
     net.forward(X, y32)
     net.forward(X, y16, bf16=True)
     assert float((y32 - y16).abs().max()) <= 3e-2 * float(y32.abs().max())
+
+
+def _bf16(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("hidden,n", [(320, 3001), (320, 100), (64, 777)])
+def test_bf16_inference_matches_bf16_emulation(hidden, n):
+    """BF16 inference (hidden layers on the tiled tensor-core kernel with bias and SiLU fused,
+    ragged row counts) against a layer-by-layer emulation: inputs, weights and every hidden
+    activation rounded to BF16, products summed in FP64.  The kernel sums in FP32, so an activation
+    may round to the neighbouring BF16 value; 5e-3 of max|y| bounds that and fails for any
+    misplaced fragment or row."""
+    net = fh.WSNet(hidden, 3, seed=5)
+    rng = np.random.default_rng(6)
+    X = rng.uniform(-1, 1, (n, 6)).astype(np.float32)
+    y16 = torch.empty(n, dtype=torch.float32, device=DEV)
+    net.forward(torch.as_tensor(X, device=DEV), y16, bf16=True)
+    layers = nn.unpack(net.get_params().astype(np.float64), nn.widths(hidden, 3))
+    a = _bf16(X)
+    for l, (W, b) in enumerate(layers):
+        z = a @ _bf16(W).T + b
+        if l < len(layers) - 1:
+            a = _bf16((z / (1.0 + np.exp(-z))).astype(np.float32))
+        else:
+            a = z
+    y = a[:, 0]
+    assert float(np.max(np.abs(y16.cpu().numpy() - y))) <= 5e-3 * float(np.max(np.abs(y)))
 
 
 def test_training_pairs_match_mode_solutions():

@@ -91,6 +91,20 @@ int fhmg_hmatrix_mesh(fhmg_hmatrix h, double* t_out, double* dmm_out);
 int fhmg_hmatrix_dense(fhmg_hmatrix h, double* R_out);
 /* Algorithmic FP64 flops of one H-matvec (Algorithm 3) or line solve (Algorithm 4) per column. */
 int fhmg_hmatrix_flops(fhmg_hmatrix h, double* flops_per_column);
+/* Host only: the digit tiles of R~ that the outer defect of defect arithmetic 2 multiplies
+ * (fhmg_problem_set_defect_arith), for inspection and tests.  Needs M a multiple of 128 and
+ * M <= 512 (else EINVAL).  Row m of the dense R~ (fhmg_hmatrix_dense) is rounded to the integers
+ * X_mk = round(R~_mk 2^{49 - E_m}), E_m the binary exponent of max_k |R~_mk| (frexp: 2^{E_m - 1} <=
+ * max < 2^{E_m}; 0 for a zero row), and written as X_mk = sum_{a=0..6} d_a 2^{7 (6 - a)} with
+ * balanced digits: d_1..d_6 in [-64, 63], |d_0| <= 129.  Blocks (I, J) of 128 time rows x 64 time
+ * levels, I = 0..M/128-1, J = 0..2I+1 (the blocks that meet the lower triangle), in I-major order;
+ * for each the digit tiles with a nonzero entry, in digit order, each 128 x 64 BF16 values (8192
+ * uint16 bit patterns, exact small integers) in the tensor cores' K-major 128-byte-swizzled
+ * layout: entry (r, k) at uint16 index (r/8)*512 + (r%8)*64 + (((k/8) ^ (r%8)) & 7)*8 + k%8.
+ * tiles: *n_tiles * 8192 values, or NULL to query *n_tiles only; pairs: 4 ints per block
+ * {digit mask, index of its first tile, 0, 0} (may be NULL); rexp: the M exponents E_m (may be
+ * NULL). */
+int fhmg_hmatrix_split_digits(fhmg_hmatrix h, unsigned short* tiles, long long* n_tiles, int* pairs, int* rexp);
 int fhmg_hmatrix_destroy(fhmg_hmatrix h);
 /* Two-grid convergence factor predicted by mode analysis (Section 5, the SAMA column of Table 2):
  * sine modes in space (a mode and its partner N+1-k per dimension: 2x2 groups in 1D, 4x4 in 2D),
@@ -226,11 +240,13 @@ int fhmg_problem_set_rtol_reference(fhmg_problem p, int ref);
  * GB300 outruns the 1/64-rate FP64 pipe; the stencil part and r = F - ... in FP64.  2 (the default
  * where available: mixed problems with M a multiple of 128 and M <= 512): the outer defect on the
  * tcgen05 tensor cores by error-free digit splitting (Ozaki et al. 2012) -- R~ (dense) and u are split
- * per time row / per grid point into 7 base-2^7 digits of 49 bits, the digit products are summed
- * exactly in FP32 tensor memory per digit-sum group, the groups are combined in double-float and
- * the stencil in 64-bit fixed point; the error of (R~ u)_{m,c} is below
- * (m+1) 2^{E_m + F_c - 46} + 2^-46 |(R~ u)_{m,c}| (2^E_m > max_k |R~_mk|, 2^F_c > max_k |u_kc|).
- * The mode solves use double-float in modes 1 and 2.  EINVAL for mode 2 where it is not available. */
+ * per time row / per grid point into 7 base-2^7 digits of 49 bits (fhmg_hmatrix_split_digits), the
+ * digit products are summed exactly in FP32 tensor memory per digit-sum group and the groups are
+ * combined in double-float; the stencil part B = F - A_h u is formed by a pre-pass in FP64 (every
+ * third time level exactly, in 64-bit fixed point).  For time row m = 0..M-1 and grid point c,
+ * |r - r_exact| <= (m+2) 2^{E_m + F_c - 46} + 2^-45 (|R~| |u|)_{m,c} + 2^-50 ((|A_h| |u|)_{m,c} + |F_{m,c}|)
+ * (2^E_m > max_k |R~_mk|, 2^F_c > max_k |u_kc|).  The mode solves use double-float in modes 1 and 2.
+ * EINVAL for mode 2 where it is not available. */
 int fhmg_problem_set_defect_arith(fhmg_problem p, int mode);
 /* BF16 tensor-core flops that one defect of defect arithmetic 2 executes per grid point (the
  * digit-tile products of the split factors, all-zero R~ digit tiles left out); EINVAL where the

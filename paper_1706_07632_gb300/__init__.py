@@ -36,6 +36,7 @@ _SIGS = {
     "fhmg_hmatrix_mesh": (_I, [_P, _P, _P]),
     "fhmg_hmatrix_dense": (_I, [_P, _P]),
     "fhmg_hmatrix_flops": (_I, [_P, _c.POINTER(_D)]),
+    "fhmg_hmatrix_split_digits": (_I, [_P, _P, _c.POINTER(_LL), _P, _P]),
     "fhmg_hmatrix_destroy": (_I, [_P]),
     "fhmg_sama_two_grid": (_I, [_P, _I, _I, _D, _I, _I, _c.POINTER(_D)]),
     "fhmg_problem_create": (_I, [_P, _I, _I, _D, _I, _P, _c.POINTER(_P)]),
@@ -172,6 +173,21 @@ class HMatrix:
         v = _D()
         _check(lib().fhmg_hmatrix_flops(self._h, ctypes.byref(v)))
         return v.value
+
+    def split_digits(self):
+        """fhmg_hmatrix_split_digits: (tiles, pairs, rexp) -- the BF16 digit tiles of R~ as uint16 bit
+        patterns (n_tiles x 8192, K-major 128-byte-swizzled 128 x 64 tiles), the per-block table
+        (n_blocks x 4: digit mask, first tile, 0, 0) and the row exponents E_m."""
+        import numpy as np
+        n = _LL(0)
+        _check(lib().fhmg_hmatrix_split_digits(self._h, None, ctypes.byref(n), None, None))
+        nI = self.M // 128
+        tiles = np.empty((n.value, 8192), dtype=np.uint16)
+        pairs = np.empty((nI * (nI + 1), 4), dtype=np.int32)
+        rexp = np.empty(self.M, dtype=np.int32)
+        _check(lib().fhmg_hmatrix_split_digits(self._h, tiles.ctypes.data, ctypes.byref(n), pairs.ctypes.data,
+                                               rexp.ctypes.data))
+        return tiles, pairs, rexp
 
     def sama_two_grid(self, dim, N, Lx=1.0, nu1=0, nu2=1):
         """Two-grid convergence factor predicted by mode analysis (fhmg_sama_two_grid)."""

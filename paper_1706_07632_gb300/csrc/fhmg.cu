@@ -1087,6 +1087,27 @@ int fhmg_hmatrix_flops(fhmg_hmatrix h, double* flops_per_column) {
   return FHMG_OK;
 }
 
+int fhmg_hmatrix_split_digits(fhmg_hmatrix h, unsigned short* tiles, long long* n_tiles, int* pairs, int* rexp) {
+  if (!h || !n_tiles) return fail(FHMG_EINVAL, "null argument");
+  const int M = h->host.M;
+  if (M % fhmg::kSplitRows != 0 || M > fhmg::kSplitMaxM)
+    return fail(FHMG_EINVAL, "digit splitting needs M a multiple of %d and M <= %d (M = %d)", fhmg::kSplitRows,
+                fhmg::kSplitMaxM, M);
+  std::vector<double> D;
+  dense_of(h->host, D);
+  fhmg::SplitHost sp;
+  fhmg::build_split(D, M, sp);
+  const long long nt = (long long)(sp.tiles.size() / ((size_t)fhmg::kSplitRows * 64));
+  if (tiles) {
+    if (*n_tiles < nt) return fail(FHMG_EINVAL, "tiles holds %lld tiles, %lld needed", *n_tiles, nt);
+    std::memcpy(tiles, sp.tiles.data(), sizeof(uint16_t) * sp.tiles.size());
+  }
+  *n_tiles = nt;
+  if (pairs) std::memcpy(pairs, sp.pairs.data(), sizeof(int) * sp.pairs.size());
+  if (rexp) std::memcpy(rexp, sp.rexp.data(), sizeof(int) * sp.rexp.size());
+  return FHMG_OK;
+}
+
 int fhmg_sama_two_grid(fhmg_hmatrix h, int dim, int N, double Lx, int nu1, int nu2, double* rho_out) {
   if (!h || !rho_out) return fail(FHMG_EINVAL, "null argument");
   if (dim != 1 && dim != 2) return fail(FHMG_EINVAL, "dim must be 1 or 2");

@@ -101,9 +101,10 @@ int fhmg_hmatrix_flops(fhmg_hmatrix h, double* flops_per_column);
  * for each the digit tiles with a nonzero entry, in digit order, each 128 x 64 BF16 values (8192
  * uint16 bit patterns, exact small integers) in the tensor cores' K-major 128-byte-swizzled
  * layout: entry (r, k) at uint16 index (r/8)*512 + (r%8)*64 + (((k/8) ^ (r%8)) & 7)*8 + k%8.
- * tiles: *n_tiles * 8192 values, or NULL to query *n_tiles only; pairs: 4 ints per block
- * {digit mask, index of its first tile, 0, 0} (may be NULL); rexp: the M exponents E_m (may be
- * NULL). */
+ * tiles: NULL to query the tile count into *n_tiles; otherwise a host buffer of *n_tiles * 8192
+ * values (*n_tiles on entry is its capacity in tiles, EINVAL if too small; on return the count
+ * written).  pairs: 4 ints per block {digit mask, index of its first tile, 0, 0}, M/128 (M/128 + 1)
+ * blocks (may be NULL); rexp: the M exponents E_m (may be NULL).  Caller-owned host memory. */
 int fhmg_hmatrix_split_digits(fhmg_hmatrix h, unsigned short* tiles, long long* n_tiles, int* pairs, int* rexp);
 int fhmg_hmatrix_destroy(fhmg_hmatrix h);
 /* Two-grid convergence factor predicted by mode analysis (Section 5, the SAMA column of Table 2):

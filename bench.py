@@ -602,7 +602,7 @@ def roofline_smoother(H, cnt, ms_total, ncols, M, hbm_peak, bf16_peak, peak_kind
 
 
 def roofline_defect(H, cnt, ms_total, ncols, M, split_flops, bf16_peak, peak_kind):
-    """The outer FP64-accurate defect, timed live (the split_colexp pass and the defect kernel).
+    """The outer FP64-accurate defect, timed live (the split_prep_kernel pass and the defect kernel).
     With digit splitting (split_flops: BF16 tensor flops per grid point of the digit-tile products)
     it is bounded by the tensor pipe; the double-float walk by the FP32 pipe."""
     n = max(cnt["defect_launches"], 1)

@@ -228,6 +228,17 @@ int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f,
  * ms).  (The tensor-core walks need leaf 64; smaller leaves trade them for fewer near-field entries.) */
 int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, int dim, int N, double Lx,
                        int prec, void* stream, int* best_leaf, double* best_ms);
+/* Host only: the H-matrix form for (alpha, gamma, T, M, leaf) with the fewest H-matvec flops per
+ * column (Algorithm 3; the FP64 walks run FP64-pipe-bound, so their time follows these flops) whose
+ * row-relative error max_m max_j |R~_mj - R_mj| / max_j |R_mj| against the exact R (every entry,
+ * Section 2) is at most err_target.  Candidates: the paper's Taylor factors with k = 4, 6, 8, 10,
+ * 12, 16, 20 terms (Section 3), Taylor factors recompressed to tol = 1e-6 .. 1e-14, and R itself
+ * (rank 0, tol 0: always admissible).  Writes the choice as the (rank, tol) arguments of
+ * fhmg_build_hmatrix, and its error and flops per column (either of those two may be NULL).
+ * EINVAL for invalid arguments or err_target < 0.  Builds every candidate on the host (seconds at
+ * M = 4096). */
+int fhmg_autotune_hmatrix(double alpha, double gamma, double T, int M, int leaf, double err_target, int* best_rank,
+                          double* best_tol, double* best_err, double* best_flops);
 /* Stopping reference of fhmg_solve: 0 (default) ||r_k|| <= rtol ||r_0|| (the paper's test, §5);
  * 1 ||r_k|| <= rtol max|F| -- the same absolute target whatever the initial guess, used to compare
  * a warm start with the zero initial guess fairly. */

@@ -37,6 +37,8 @@ _SIGS = {
     "fhmg_hmatrix_dense": (_I, [_P, _P]),
     "fhmg_hmatrix_flops": (_I, [_P, _c.POINTER(_D)]),
     "fhmg_hmatrix_split_digits": (_I, [_P, _P, _c.POINTER(_LL), _P, _P]),
+    "fhmg_autotune_hmatrix": (_I, [_D, _D, _D, _I, _I, _D, _c.POINTER(_I), _c.POINTER(_D), _c.POINTER(_D),
+                                  _c.POINTER(_D)]),
     "fhmg_hmatrix_destroy": (_I, [_P]),
     "fhmg_sama_two_grid": (_I, [_P, _I, _I, _D, _I, _I, _c.POINTER(_D)]),
     "fhmg_problem_create": (_I, [_P, _I, _I, _D, _I, _P, _c.POINTER(_P)]),
@@ -454,3 +456,13 @@ def autotune_leaf(alpha, gamma, T, M, tol, dim, N, Lx=1.0, prec=FP64, stream=Non
     _check(lib().fhmg_autotune_leaf(alpha, gamma, T, M, tol, dim, N, Lx, prec, _stream_ptr(stream),
                                     ctypes.byref(leaf), ctypes.byref(ms)))
     return leaf.value, ms.value
+
+
+def autotune_hmatrix(alpha, gamma, T, M, leaf=64, err_target=1e-10):
+    """fhmg_autotune_hmatrix (host only): the (rank, tol) of fhmg_build_hmatrix with the fewest
+    H-matvec flops per column whose row-relative error against the exact R is <= err_target, as
+    {"rank", "tol", "err", "flops_per_column"}."""
+    r, t, e, f = _I(), _D(), _D(), _D()
+    _check(lib().fhmg_autotune_hmatrix(alpha, gamma, T, M, leaf, err_target, ctypes.byref(r), ctypes.byref(t),
+                                       ctypes.byref(e), ctypes.byref(f)))
+    return {"rank": r.value, "tol": t.value, "err": e.value, "flops_per_column": f.value}

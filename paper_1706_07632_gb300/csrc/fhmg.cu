@@ -1813,6 +1813,61 @@ int fhmg_solve_batched(int n, fhmg_problem* probs, double** u, const double** f,
   return FHMG_OK;
 }
 
+int fhmg_autotune_hmatrix(double alpha, double gamma, double T, int M, int leaf, double err_target, int* best_rank,
+                          double* best_tol, double* best_err, double* best_flops) {
+  if (!best_rank || !best_tol) return fail(FHMG_EINVAL, "null argument");
+  if (!(err_target >= 0.0)) return fail(FHMG_EINVAL, "err_target must be >= 0");
+  // the exact reference: every entry of R (dense mode)
+  fhmg::HostH ref;
+  if (fhmg::build_hmatrix(alpha, gamma, T, M, leaf, 0, 0.0, ref) != 0)
+    return fail(FHMG_EINVAL, "invalid arguments: need 0<alpha<1, gamma>=1, T>0, M = leaf*2^p, leaf in {16,32,64}");
+  std::vector<double> R;
+  dense_of(ref, R);
+  std::vector<double> rowmax((size_t)M, 0.0);
+  for (int m = 0; m < M; ++m)
+    for (int j = 0; j <= m; ++j) rowmax[m] = std::max(rowmax[m], std::fabs(R[(size_t)m * M + j]));
+  // candidates: the paper's Taylor form with k terms, then Taylor + recompression to tol, then R itself
+  struct Cand {
+    int rank;
+    double tol;
+  };
+  static const Cand cands[] = {{4, 0.0},   {6, 0.0},    {8, 0.0},     {10, 0.0},    {12, 0.0},    {16, 0.0}, {20, 0.0},
+                               {0, 1e-6}, {0, 1e-8}, {0, 1e-10}, {0, 1e-12}, {0, 1e-14}, {0, 0.0}};
+  int br = -1;
+  double bt = 0.0, be = 0.0, bf = 0.0;
+  std::vector<double> D;
+  for (const Cand& c : cands) {
+    fhmg::HostH h;
+    double err = 0.0;
+    fhmg::FlatH f;
+    if (c.rank == 0 && c.tol == 0.0) {
+      fhmg::flatten(ref, f);  // R itself: exact
+    } else {
+      if (fhmg::build_hmatrix(alpha, gamma, T, M, leaf, c.rank, c.tol, h) != 0) continue;
+      fhmg::flatten(h, f);
+      dense_of(h, D);
+      for (int m = 0; m < M; ++m) {
+        if (rowmax[m] == 0.0) continue;
+        double e = 0.0;
+        for (int j = 0; j <= m; ++j) e = std::max(e, std::fabs(D[(size_t)m * M + j] - R[(size_t)m * M + j]));
+        err = std::max(err, e / rowmax[m]);
+      }
+    }
+    const double fl = (double)f.flops_per_col_matvec;
+    if (err <= err_target && (br < 0 || fl < bf || (fl == bf && err < be))) {
+      br = c.rank;
+      bt = c.tol;
+      be = err;
+      bf = fl;
+    }
+  }
+  *best_rank = br;
+  *best_tol = bt;
+  if (best_err) *best_err = be;
+  if (best_flops) *best_flops = bf;
+  return FHMG_OK;
+}
+
 int fhmg_autotune_leaf(double alpha, double gamma, double T, int M, double tol, int dim, int N, double Lx, int prec,
                        void* stream, int* best_leaf, double* best_ms) {
   if (!best_leaf) return fail(FHMG_EINVAL, "best_leaf is NULL");
